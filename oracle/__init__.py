@@ -1,0 +1,175 @@
+"""ctypes access to the ELSAR CPU oracle (oracle/elsar_oracle.cpp, oracle/mlp_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and the
+bench's CPU-baseline leg, never by the product package.  Shares no code with
+the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "libelsar_oracle.so")
+_SRCS = ["elsar_oracle.cpp"]
+RECORD = 100
+
+_lib = None
+
+P = ctypes.c_void_p
+U64 = ctypes.c_uint64
+U32 = ctypes.c_uint32
+I32 = ctypes.c_int
+
+
+def build():
+    srcs = [os.path.join(_HERE, s) for s in _SRCS]
+    subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC",
+                           "-o", _LIB] + srcs)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        srcs = [os.path.join(_HERE, s) for s in _SRCS]
+        if not os.path.exists(_LIB) or any(os.path.getmtime(s) > os.path.getmtime(_LIB) for s in srcs):
+            build()
+        L = ctypes.CDLL(_LIB)
+        sig = {
+            "eo_encode9": (U64, [P]),
+            "eo_encode9_records": (None, [P, U64, P]),
+            "eo_splitmix64_at": (U64, [U64, U64]),
+            "eo_default_sample_size": (U64, [U64]),
+            "eo_sample": (None, [P, U64, U64, U64, P]),
+            "eo_rmi_fit": (U64, [P, U64, U32, U32, P]),
+            "eo_rmi_export": (None, [I32, P, P, P]),
+            "eo_rmi_eval": (None, [I32, P, U64, P, P]),
+            "eo_rmi_release": (None, []),
+            "eo_sort": (I32, [P, U64, U32, U32, U32, U32, U64, U64, I32, P, P, P, P, P, P]),
+            "eo_stable_sort": (None, [P, U64, P]),
+            "eo_validate": (I32, [P, P, U64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def encode9(key: bytes) -> int:
+    buf = np.frombuffer(bytes(key[:10]).ljust(10, b" "), dtype=np.uint8).copy()
+    return int(lib().eo_encode9(buf.ctypes.data))
+
+
+def encode9_records(recs: np.ndarray) -> np.ndarray:
+    n = recs.size // RECORD
+    out = np.empty(n, dtype=np.uint64)
+    lib().eo_encode9_records(_ptr(recs), n, _ptr(out))
+    return out
+
+
+def splitmix64_at(seed: int, k: int) -> int:
+    return int(lib().eo_splitmix64_at(seed, k))
+
+
+def default_sample_size(n: int) -> int:
+    return int(lib().eo_default_sample_size(n))
+
+
+LEAF_TARGET = 16  # T: sample keys per RMI node below which it stops splitting (a node splits above 2T)
+MAX_DEPTH = 32  # Dmax
+
+
+def default_fine_log2(n: int, P: int) -> int:
+    """log2 of the fine-bin count: about 1024 records per bin, within [max(log2 P, 6), 20]."""
+    lp = P.bit_length() - 1
+    want = max(0, (max(n, 1) - 1).bit_length() - 10)
+    return max(lp, min(20, max(6, want)))
+
+
+def sample(recs: np.ndarray, S: int, seed: int) -> np.ndarray:
+    n = recs.size // RECORD
+    out = np.empty(S, dtype=np.uint64)
+    lib().eo_sample(_ptr(recs), n, S, seed, _ptr(out))
+    return out
+
+
+class Rmi:
+    """The oracle's fitted RMI, exported as breadth-first node arrays."""
+
+    def __init__(self, sorted_sample: np.ndarray, T: int = LEAF_TARGET, Dmax: int = MAX_DEPTH):
+        s = np.ascontiguousarray(sorted_sample, dtype=np.uint64)
+        self.sample, self.S = s, s.size
+        h = ctypes.c_int(-1)
+        nn = int(lib().eo_rmi_fit(_ptr(s), s.size, T, Dmax, ctypes.byref(h)))
+        if nn == 0:
+            raise ValueError("eo_rmi_fit rejected the sample")
+        self.handle = h.value
+        self.nu64 = np.zeros((nn, 4), dtype=np.uint64)
+        self.nu32 = np.zeros((nn, 3), dtype=np.uint32)
+        self.nf64 = np.zeros((nn, 7))
+        lib().eo_rmi_export(self.handle, _ptr(self.nu64), _ptr(self.nu32), _ptr(self.nf64))
+
+    def __len__(self):
+        return self.nu64.shape[0]
+
+    s_ = property(lambda self: self.nu64[:, 0])
+    e_ = property(lambda self: self.nu64[:, 1])
+    base = property(lambda self: self.nu64[:, 2])
+    child0 = property(lambda self: self.nu64[:, 3])
+    shift = property(lambda self: self.nu32[:, 0])
+    fanout = property(lambda self: self.nu32[:, 1])
+    depth = property(lambda self: self.nu32[:, 2])
+    gamma = property(lambda self: self.nf64[:, 0])
+    delta = property(lambda self: self.nf64[:, 1])
+    scale = property(lambda self: self.nf64[:, 2])
+    g = property(lambda self: self.nf64[:, 3])
+    d = property(lambda self: self.nf64[:, 4])
+    lo = property(lambda self: self.nf64[:, 5])
+    hi = property(lambda self: self.nf64[:, 6])
+
+    def eval(self, xs: np.ndarray):
+        """(F, leaf node index) at each key encoding."""
+        xs = np.ascontiguousarray(xs, dtype=np.uint64)
+        F = np.empty(xs.size)
+        leaf = np.empty(xs.size, dtype=np.uint64)
+        lib().eo_rmi_eval(self.handle, _ptr(xs), xs.size, _ptr(F), _ptr(leaf))
+        return F, leaf
+
+
+def sort(recs: np.ndarray, P: int, log2B: int, S: int, seed: int, balance: int = 1, want_detail=False,
+         T: int = LEAF_TARGET, Dmax: int = MAX_DEPTH):
+    """Run the whole oracle; returns out (and a dict of intermediate results)."""
+    n = recs.size // RECORD
+    out = np.empty_like(recs)
+    B = 1 << log2B
+    q = np.empty(n, dtype=np.uint32) if want_detail else None
+    pid = np.empty(n, dtype=np.uint32) if want_detail else None
+    off = np.empty(P + 1, dtype=np.uint64)
+    counts = np.empty(B, dtype=np.uint64) if want_detail else None
+    cuts = np.empty(P + 1, dtype=np.uint32) if want_detail else None
+    rc = lib().eo_sort(_ptr(recs), n, P, log2B, T, Dmax, S, seed, balance, _ptr(out), _ptr(q), _ptr(pid), _ptr(off),
+                       _ptr(counts), _ptr(cuts))
+    if rc:
+        raise ValueError(f"eo_sort rc={rc}")
+    if want_detail:
+        return out, dict(q=q, pid=pid, part_off=off, bin_counts=counts, cuts=cuts)
+    return out
+
+
+def stable_sort(recs: np.ndarray) -> np.ndarray:
+    out = np.empty_like(recs)
+    lib().eo_stable_sort(_ptr(recs), recs.size // RECORD, _ptr(out))
+    return out
+
+
+def validate(inp: np.ndarray, out: np.ndarray) -> int:
+    return int(lib().eo_validate(_ptr(inp), _ptr(out), inp.size // RECORD))

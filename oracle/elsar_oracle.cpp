@@ -1,0 +1,445 @@
+// ELSAR oracle: a plain, slow, single-threaded CPU restatement of the learned
+// partition-and-concatenate sort of "Parallel External Sorting of ASCII Records
+// Using Learned Models" (arXiv 2305.05671).
+//
+// TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+// bench's CPU-baseline leg may load this library.  It shares no code, header,
+// table or constant generator with the CUDA path, and it never reads a value
+// produced by it.  Every floating-point step is written out in the order the
+// functions below state, compiled with -ffp-contract=off, so nothing is fused
+// that is not an explicit std::fma.
+//
+// What it computes, step by step:
+//   encode    Sec. 4: base-95 numerical encoding of the first 9 key bytes
+//   sample    Sec. 3.1 / Sec. 6: uniform key sample, 1 % of the input, <= 10M
+//   rmi_fit   Sec. 3.1: RMI of linear regressions on the sorted sample, dense
+//             regions getting more nodes (leaf clamping keeps it monotone)
+//   classify  Sec. 3.3 / Algorithm 1 (the reader loop): p = F_X(encode(x))
+//   offsets   Sec. 3.5: write offset = sum of the sizes of earlier partitions
+//   sort      Sec. 3.4 / Sec. 4 touch-up: each partition in key byte order
+//             (memcmp), ties kept in input order
+//   concat    Sec. 3.5: partitions written back to back, no merge
+// Readings of places the paper leaves open are listed beside each function.
+//
+// Parity of this oracle is pinned by tests/test_oracle_*.py (closed forms,
+// brute force, invariants, library least squares); see those files.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace {
+
+constexpr int kRecord = 100;
+constexpr int kKey = 10;
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+// ---------------------------------------------------------------- Sec. 4
+// Character c at 1-based position i of an l-character key contributes
+// (ASCII(c) - 32) * 95^(l-i); with a 64-bit integer l = 9 (the paper's
+// log2 figure of 59.14 bits).  Reading: printable ASCII is 32..126, which is
+// what base 95 needs; bytes outside that range are clamped to it, which keeps
+// the map monotone in byte order.  The tenth key byte is left to the sort.
+uint64_t encode9(const uint8_t* key) {
+  uint64_t e = 0;
+  for (int i = 0; i < 9; ++i) {
+    int c = key[i];
+    if (c < 32) c = 32;
+    if (c > 126) c = 126;
+    e = e * 95u + (uint64_t)(c - 32);
+  }
+  return e;
+}
+
+// The k-th output of the SplitMix64 generator seeded with `seed`
+// (state advances by the golden gamma; Steele, Lea, Flood 2014).
+uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// ---------------------------------------------------------------- Sec. 3.1
+// RMI CDF model.  The paper names the architecture -- starting from the root,
+// a key walks through internal linear models, each picking a more specialised
+// model below it, until a leaf outputs y ~ P(X <= x) -- says that training
+// gives dense regions of the key domain more nodes (so that the leaves act as
+// equi-depth bins), and defers the details to the RMI literature.  Readings
+// taken here (an adaptive-depth RMI; all numbers are of the sorted sample):
+//  * A node covers sample ranks [s, e), n = e - s points.  It is a leaf if
+//    n <= 2T, if its points are all equal, if it is at depth Dmax, or if its
+//    own router would send its first and last point to the same child.
+//    Otherwise it is internal with f = ceil(n / T) children.
+//  * Every node fits ordinary least squares of local rank r = k - s on local
+//    coordinate u = (x - base) >> shift, base = its smallest sample, shift =
+//    the fewest bits that bring its span under 2^32.  The sums are formed
+//    exactly in integers (so no summation order matters); then
+//      gamma = max(0, (n*Sur - Su*Sr) / (n*Suu - Su^2))   [each side rounded once]
+//      delta = (Sr - gamma*Su) / n.
+//  * An internal node routes x to child c = clamp(floor(fma(gamma,u,delta) * f/n), 0, f-1);
+//    child c covers the ranks of the points routed to it (contiguous, since
+//    the router is monotone).  Children are numbered breadth first.
+//  * A leaf outputs F(x) = clamp(fma(gamma/S, u, (s + delta)/S), s/S, e/S):
+//    with non-negative slopes and monotone routing this makes F monotone,
+//    which concatenation needs (Eq. 1) and an unclamped RMI does not guarantee.
+//    Keys below a node's base get u = 0.
+struct Node {
+  uint64_t s = 0, e = 0, base = 0;
+  uint32_t shift = 0, fanout = 0;  // fanout 0: leaf
+  uint64_t child0 = 0;
+  uint32_t depth = 0;
+  double gamma = 0, delta = 0, scale = 0;  // scale = f / n (internal)
+  double g = 0, d = 0, lo = 0, hi = 0;     // leaf output constants
+};
+
+struct Rmi {
+  uint64_t S = 0;
+  std::vector<Node> node;
+};
+
+inline double pos_or_zero(double v) { return v > 0.0 ? v : 0.0; }
+
+inline uint64_t local_u(const Node& v, uint64_t x) { return x > v.base ? (x - v.base) >> v.shift : 0; }
+
+inline uint32_t route(const Node& v, uint64_t x) {
+  double t = std::fma(v.gamma, (double)local_u(v, x), v.delta) * v.scale;
+  if (!(t > 0.0)) return 0;
+  if (t >= (double)v.fanout) return v.fanout - 1;
+  return (uint32_t)t;
+}
+
+// exact least squares of local rank on local coordinate over sorted x[s, e)
+void fit_linear(const uint64_t* x, Node& v) {
+  uint64_t n = v.e - v.s;
+  v.base = x[v.s];
+  uint64_t span = x[v.e - 1] - v.base;
+  uint32_t bits = 0;
+  while (bits < 64 && (span >> bits) != 0) ++bits;
+  v.shift = bits > 32 ? bits - 32 : 0;
+  u128 Su = 0, Suu = 0, Sur = 0;
+  for (uint64_t k = v.s; k < v.e; ++k) {
+    u128 u = (x[k] - v.base) >> v.shift;
+    Su += u;
+    Suu += u * u;
+    Sur += u * (u128)(k - v.s);
+  }
+  i128 nn = (i128)n;
+  i128 Sr = nn * (nn - 1) / 2;
+  i128 Duu = nn * (i128)Suu - (i128)Su * (i128)Su;
+  i128 Dur = nn * (i128)Sur - (i128)Su * Sr;
+  v.gamma = (n >= 2 && Duu > 0) ? pos_or_zero((double)Dur / (double)Duu) : 0.0;
+  v.delta = ((double)Sr - v.gamma * (double)Su) / (double)n;
+}
+
+void make_leaf(Node& v, uint64_t S) {
+  v.fanout = 0;
+  v.scale = 0.0;
+  v.lo = (double)v.s / (double)S;
+  v.hi = (double)v.e / (double)S;
+  if (v.e == v.s) {
+    v.base = 0;
+    v.shift = 0;
+    v.gamma = 0.0;
+    v.delta = 0.0;
+    v.g = 0.0;
+    v.d = v.lo;
+    return;
+  }
+  v.g = v.gamma / (double)S;
+  v.d = ((double)v.s + v.delta) / (double)S;
+}
+
+Rmi rmi_fit(const uint64_t* x, uint64_t S, uint32_t T, uint32_t Dmax) {
+  Rmi m;
+  m.S = S;
+  Node root;
+  root.s = 0;
+  root.e = S;
+  m.node.push_back(root);
+  for (size_t i = 0; i < m.node.size(); ++i) {  // breadth-first
+    Node v = m.node[i];
+    uint64_t n = v.e - v.s;
+    if (n == 0) {
+      make_leaf(v, S);
+      m.node[i] = v;
+      continue;
+    }
+    fit_linear(x, v);
+    bool split = n > 2ull * T && v.depth < Dmax && x[v.s] < x[v.e - 1];
+    if (split) {
+      v.fanout = (uint32_t)((n + T - 1) / T);
+      v.scale = (double)v.fanout / (double)n;
+      if (route(v, x[v.s]) == route(v, x[v.e - 1])) split = false;
+    }
+    if (!split) {
+      make_leaf(v, S);
+      m.node[i] = v;
+      continue;
+    }
+    v.child0 = m.node.size();
+    std::vector<uint64_t> cs(v.fanout + 1, v.e);
+    uint64_t k = v.s;
+    for (uint32_t c = 0; c < v.fanout; ++c) {
+      while (k < v.e && route(v, x[k]) < c) ++k;
+      cs[c] = k;
+    }
+    m.node[i] = v;
+    for (uint32_t c = 0; c < v.fanout; ++c) {
+      Node ch;
+      ch.s = cs[c];
+      ch.e = cs[c + 1];
+      ch.depth = v.depth + 1;
+      m.node.push_back(ch);
+    }
+  }
+  return m;
+}
+
+uint64_t find_leaf(const Rmi& m, uint64_t x) {
+  uint64_t i = 0;
+  while (m.node[i].fanout) i = m.node[i].child0 + route(m.node[i], x);
+  return i;
+}
+
+double rmi_cdf(const Rmi& m, uint64_t x) {
+  const Node& v = m.node[find_leaf(m, x)];
+  double y = std::fma(v.g, (double)local_u(v, x), v.d);
+  if (y < v.lo) return v.lo;
+  if (y > v.hi) return v.hi;
+  return y;
+}
+
+// ---------------------------------------------------------------- Sec. 3.3
+// Fine bin q = min(B-1, floor(B * F)).  Paper rule (Algorithm 1, reader loop):
+// partition p = min(P-1, floor(P * F)), i.e. q / (B/P) for powers of two.
+// Refined rule (an addition of this library, not the paper's): the cut c_p of
+// partition p is the fine-bin boundary t whose exact cumulative count C(t) is
+// closest to p*N/P (ties to the smaller t); partition p = bins [c_p, c_{p+1}).
+inline uint32_t fine_bin(double F, uint32_t log2B) {
+  uint32_t B = 1u << log2B;
+  uint32_t q = (uint32_t)(F * (double)B);
+  return q < B ? q : B - 1;
+}
+
+std::vector<uint32_t> cuts_of(const std::vector<uint64_t>& counts, uint32_t P, uint32_t log2B, uint64_t N,
+                              int balance) {
+  uint32_t B = 1u << log2B;
+  std::vector<uint32_t> c(P + 1);
+  c[0] = 0;
+  c[P] = B;
+  if (!balance) {
+    for (uint32_t p = 1; p < P; ++p) c[p] = p * (B / P);
+    return c;
+  }
+  std::vector<uint64_t> C(B + 1, 0);
+  for (uint32_t t = 0; t < B; ++t) C[t + 1] = C[t] + counts[t];
+  for (uint32_t p = 1; p < P; ++p) {
+    int64_t target = (int64_t)p * (int64_t)N;
+    uint32_t best = 0;
+    int64_t bestd = -1;
+    for (uint32_t t = 0; t <= B; ++t) {
+      int64_t d = (int64_t)P * (int64_t)C[t] - target;
+      if (d < 0) d = -d;
+      if (bestd < 0 || d < bestd) {
+        bestd = d;
+        best = t;
+      }
+    }
+    c[p] = best;
+  }
+  return c;
+}
+
+inline uint32_t pid_of(const std::vector<uint32_t>& c, uint32_t P, uint32_t q) {
+  uint32_t p = 0;
+  for (uint32_t k = 1; k < P; ++k)
+    if (c[k] <= q) ++p;
+  return p;
+}
+
+bool key_less(const uint8_t* recs, uint64_t a, uint64_t b) {
+  return std::memcmp(recs + a * kRecord, recs + b * kRecord, kKey) < 0;
+}
+
+void stable_sort_indices(const uint8_t* recs, std::vector<uint64_t>& idx) {
+  std::stable_sort(idx.begin(), idx.end(), [recs](uint64_t a, uint64_t b) { return key_less(recs, a, b); });
+}
+
+uint64_t parse_index(const uint8_t* rec, bool* ok) {
+  uint64_t v = 0;
+  *ok = true;
+  for (int j = 0; j < 32; ++j) {
+    int c = rec[kKey + j];
+    int d;
+    if (c >= '0' && c <= '9') d = c - '0';
+    else if (c >= 'A' && c <= 'F') d = c - 'A' + 10;
+    else { *ok = false; return 0; }
+    if (j < 16) { if (d) *ok = false; continue; }
+    v = (v << 4) | (uint64_t)d;
+  }
+  return v;
+}
+
+}  // namespace
+
+extern "C" {
+
+uint64_t eo_encode9(const uint8_t* key) { return encode9(key); }
+
+void eo_encode9_records(const uint8_t* recs, uint64_t n, uint64_t* out) {
+  for (uint64_t i = 0; i < n; ++i) out[i] = encode9(recs + i * kRecord);
+}
+
+uint64_t eo_splitmix64_at(uint64_t seed, uint64_t k) { return splitmix64_at(seed, k); }
+
+// Sec. 3.1 / Sec. 6: 1 % of the input, at least 1000 keys, at most 10M.
+// Reading: drawn uniformly over the whole input (not only the first batch of
+// one reader thread), with replacement: position k is mulhi64(SplitMix64_k(seed), n).
+uint64_t eo_default_sample_size(uint64_t n) {
+  if (n == 0) return 0;
+  uint64_t s = (n + 99) / 100;
+  if (s < 1000) s = 1000;
+  if (s > 10000000) s = 10000000;
+  return s;
+}
+
+void eo_sample(const uint8_t* recs, uint64_t n, uint64_t S, uint64_t seed, uint64_t* out_enc) {
+  for (uint64_t k = 0; k < S; ++k) {
+    uint64_t i = (uint64_t)(((u128)splitmix64_at(seed, k) * (u128)n) >> 64);
+    out_enc[k] = encode9(recs + i * kRecord);
+  }
+}
+
+// Fit on a sorted sample.  Returns the node count, or 0 on bad input.
+// The fitted model stays in a small handle table for export and evaluation.
+static std::vector<Rmi> g_models;
+
+uint64_t eo_rmi_fit(const uint64_t* sorted, uint64_t S, uint32_t T, uint32_t Dmax, int* handle) {
+  if (T < 1 || S >= (1ull << 24)) return 0;
+  for (uint64_t k = 1; k < S; ++k)
+    if (sorted[k - 1] > sorted[k]) return 0;
+  g_models.push_back(rmi_fit(sorted, S, T, Dmax));
+  *handle = (int)g_models.size() - 1;
+  return g_models.back().node.size();
+}
+
+// Node arrays: u64[4] {s, e, base, child0}; u32[3] {shift, fanout, depth};
+// f64[7] {gamma, delta, scale, g, d, lo, hi}.
+void eo_rmi_export(int handle, uint64_t* nu64, uint32_t* nu32, double* nf64) {
+  const Rmi& m = g_models[handle];
+  for (size_t i = 0; i < m.node.size(); ++i) {
+    const Node& v = m.node[i];
+    nu64[4 * i + 0] = v.s;
+    nu64[4 * i + 1] = v.e;
+    nu64[4 * i + 2] = v.base;
+    nu64[4 * i + 3] = v.child0;
+    nu32[3 * i + 0] = v.shift;
+    nu32[3 * i + 1] = v.fanout;
+    nu32[3 * i + 2] = v.depth;
+    double f[7] = {v.gamma, v.delta, v.scale, v.g, v.d, v.lo, v.hi};
+    for (int t = 0; t < 7; ++t) nf64[7 * i + t] = f[t];
+  }
+}
+
+void eo_rmi_eval(int handle, const uint64_t* xs, uint64_t m, double* F, uint64_t* leaf) {
+  const Rmi& r = g_models[handle];
+  for (uint64_t i = 0; i < m; ++i) {
+    if (F) F[i] = rmi_cdf(r, xs[i]);
+    if (leaf) leaf[i] = find_leaf(r, xs[i]);
+  }
+}
+
+void eo_rmi_release(void) { g_models.clear(); }
+
+// The whole method (Algorithm 1 without its files):
+//   sample -> sort sample -> fit -> per record q, pid -> partition lists in
+//   input order -> stable sort each by memcmp -> concatenate.
+// Optional outputs (nullable): q[n], pid[n], part_off[P+1], bin_counts[B], cuts[P+1].
+int eo_sort(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint32_t T, uint32_t Dmax, uint64_t S,
+            uint64_t seed, int balance, uint8_t* out, uint32_t* q_out, uint32_t* pid_out, uint64_t* part_off, uint64_t* bin_counts,
+            uint32_t* cuts_out) {
+  if (P < 1 || (P & (P - 1)) || log2B > 24 || (1u << log2B) < P || T < 1) return 1;
+  if (S >= (1ull << 24) || (n > 0 && S == 0)) return 1;  // exact sums need S < 2^24
+  if (n == 0) {
+    if (part_off)
+      for (uint32_t p = 0; p <= P; ++p) part_off[p] = 0;
+    return 0;
+  }
+  std::vector<uint64_t> sample(S);
+  eo_sample(in, n, S, seed, sample.data());
+  std::sort(sample.begin(), sample.end());
+  Rmi m = rmi_fit(sample.data(), S, T, Dmax);
+  uint32_t B = 1u << log2B;
+  std::vector<uint32_t> q(n);
+  std::vector<uint64_t> counts(B, 0);
+  for (uint64_t i = 0; i < n; ++i) {
+    q[i] = fine_bin(rmi_cdf(m, encode9(in + i * kRecord)), log2B);
+    counts[q[i]]++;
+  }
+  std::vector<uint32_t> c = cuts_of(counts, P, log2B, n, balance);
+  std::vector<uint32_t> pid_of_bin(B);
+  for (uint32_t t = 0; t < B; ++t) pid_of_bin[t] = pid_of(c, P, t);
+  std::vector<std::vector<uint64_t>> part(P);
+  for (uint64_t i = 0; i < n; ++i) part[pid_of_bin[q[i]]].push_back(i);
+  uint64_t off = 0;
+  for (uint32_t p = 0; p < P; ++p) {
+    if (part_off) part_off[p] = off;
+    stable_sort_indices(in, part[p]);
+    for (uint64_t i : part[p]) {
+      std::memcpy(out + off * kRecord, in + i * kRecord, kRecord);
+      ++off;
+    }
+  }
+  if (part_off) part_off[P] = off;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (q_out) q_out[i] = q[i];
+    if (pid_out) pid_out[i] = pid_of_bin[q[i]];
+  }
+  if (bin_counts)
+    for (uint32_t t = 0; t < B; ++t) bin_counts[t] = counts[t];
+  if (cuts_out)
+    for (uint32_t p = 0; p <= P; ++p) cuts_out[p] = c[p];
+  return 0;
+}
+
+// The plain definition of the result: all records stably sorted by memcmp on
+// the 10-byte key (Sec. 7.1 methodology: byte order as memcmp/strncmp).
+void eo_stable_sort(const uint8_t* in, uint64_t n, uint8_t* out) {
+  std::vector<uint64_t> idx(n);
+  for (uint64_t i = 0; i < n; ++i) idx[i] = i;
+  stable_sort_indices(in, idx);
+  for (uint64_t k = 0; k < n; ++k) std::memcpy(out + k * kRecord, in + idx[k] * kRecord, kRecord);
+}
+
+// valsort analogue (Sec. 7.1): returns 0 if `out` is a sorted, stable
+// permutation of `in`, else a bit mask: 1 unsorted, 2 not a permutation
+// (unparsable/duplicate/out-of-range index, or bytes differ from in[index]),
+// 4 equal keys out of input order.  Records carry their input index in hex.
+int eo_validate(const uint8_t* in, const uint8_t* out, uint64_t n) {
+  int bad = 0;
+  std::vector<uint8_t> seen(n, 0);
+  uint64_t prev_idx = 0;
+  for (uint64_t k = 0; k < n; ++k) {
+    const uint8_t* r = out + k * kRecord;
+    bool ok;
+    uint64_t idx = parse_index(r, &ok);
+    if (!ok || idx >= n || seen[idx] || std::memcmp(r, in + idx * kRecord, kRecord) != 0) {
+      bad |= 2;
+    } else {
+      seen[idx] = 1;
+    }
+    if (k > 0) {
+      int c = std::memcmp(out + (k - 1) * kRecord, r, kKey);
+      if (c > 0) bad |= 1;
+      if (c == 0 && ok && idx < prev_idx) bad |= 4;
+    }
+    prev_idx = idx;
+  }
+  return bad;
+}
+
+}  // extern "C"
