@@ -40,16 +40,21 @@ typedef __int128 i128;
 // ---------------------------------------------------------------- Sec. 4
 // Character c at 1-based position i of an l-character key contributes
 // (ASCII(c) - 32) * 95^(l-i); with a 64-bit integer l = 9 (the paper's
-// log2 figure of 59.14 bits).  Reading: printable ASCII is 32..126, which is
-// what base 95 needs; bytes outside that range are clamped to it, which keeps
-// the map monotone in byte order.  The tenth key byte is left to the sort.
+// log2 figure of 59.14 bits).  Printable ASCII is 32..126, which is what
+// base 95 needs.  The paper leaves other bytes out; reading taken here so that
+// the encoding stays monotone in byte order (Eq. 1) for any byte string: at
+// the first byte below 32 (above 126) that digit and every later digit become
+// 0 (94) -- the key encodes as the smallest (largest) printable key with its
+// printable prefix.  The tenth key byte is left to the sort.
 uint64_t encode9(const uint8_t* key) {
   uint64_t e = 0;
+  int sat = 0;  // 0: none yet, 1: saturate low, 2: saturate high
   for (int i = 0; i < 9; ++i) {
     int c = key[i];
-    if (c < 32) c = 32;
-    if (c > 126) c = 126;
-    e = e * 95u + (uint64_t)(c - 32);
+    if (sat == 0 && c < 32) sat = 1;
+    if (sat == 0 && c > 126) sat = 2;
+    int d = sat == 1 ? 0 : (sat == 2 ? 94 : c - 32);
+    e = e * 95u + (uint64_t)d;
   }
   return e;
 }
@@ -73,7 +78,9 @@ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
 //  * A node covers sample ranks [s, e), n = e - s points.  It is a leaf if
 //    n <= 2T, if its points are all equal, if it is at depth Dmax, or if its
 //    own router would send its first and last point to the same child.
-//    Otherwise it is internal with f = ceil(n / T) children.
+//    Otherwise it is internal with f = ceil(n / T) children -- unless the
+//    children of its whole level would take the tree past 4*ceil(S/T) + 1024
+//    nodes, in which case every node of that level is a leaf.
 //  * Every node fits ordinary least squares of local rank r = k - s on local
 //    coordinate u = (x - base) >> shift, base = its smallest sample, shift =
 //    the fewest bits that bring its span under 2^32.  The sums are formed
@@ -153,6 +160,10 @@ void make_leaf(Node& v, uint64_t S) {
   v.d = ((double)v.s + v.delta) / (double)S;
 }
 
+// Node budget: a level's nodes split only if the tree then still has at most
+// 4*ceil(S/T) + 1024 nodes; otherwise every node of that level is a leaf.
+uint64_t node_budget(uint64_t S, uint32_t T) { return 4 * ((S + T - 1) / T) + 1024; }
+
 Rmi rmi_fit(const uint64_t* x, uint64_t S, uint32_t T, uint32_t Dmax) {
   Rmi m;
   m.S = S;
@@ -160,41 +171,50 @@ Rmi rmi_fit(const uint64_t* x, uint64_t S, uint32_t T, uint32_t Dmax) {
   root.s = 0;
   root.e = S;
   m.node.push_back(root);
-  for (size_t i = 0; i < m.node.size(); ++i) {  // breadth-first
-    Node v = m.node[i];
-    uint64_t n = v.e - v.s;
-    if (n == 0) {
-      make_leaf(v, S);
+  size_t lv0 = 0, lv1 = 1;  // nodes of the current level, numbered breadth first
+  while (lv0 < lv1) {
+    std::vector<bool> split(lv1 - lv0, false);
+    uint64_t children = 0;
+    for (size_t i = lv0; i < lv1; ++i) {
+      Node& v = m.node[i];
+      uint64_t n = v.e - v.s;
+      if (n == 0) continue;
+      fit_linear(x, v);
+      bool sp = n > 2ull * T && v.depth < Dmax && x[v.s] < x[v.e - 1];
+      if (sp) {
+        v.fanout = (uint32_t)((n + T - 1) / T);
+        v.scale = (double)v.fanout / (double)n;
+        if (route(v, x[v.s]) == route(v, x[v.e - 1])) sp = false;
+        if (!sp) v.fanout = 0;
+      }
+      split[i - lv0] = sp;
+      if (sp) children += v.fanout;
+    }
+    const bool room = m.node.size() + children <= node_budget(S, T);
+    for (size_t i = lv0; i < lv1; ++i) {
+      if (!(room && split[i - lv0])) {
+        make_leaf(m.node[i], S);
+        continue;
+      }
+      Node v = m.node[i];
+      v.child0 = m.node.size();
+      std::vector<uint64_t> cs(v.fanout + 1, v.e);
+      uint64_t k = v.s;
+      for (uint32_t c = 0; c < v.fanout; ++c) {
+        while (k < v.e && route(v, x[k]) < c) ++k;
+        cs[c] = k;
+      }
       m.node[i] = v;
-      continue;
+      for (uint32_t c = 0; c < v.fanout; ++c) {
+        Node ch;
+        ch.s = cs[c];
+        ch.e = cs[c + 1];
+        ch.depth = v.depth + 1;
+        m.node.push_back(ch);
+      }
     }
-    fit_linear(x, v);
-    bool split = n > 2ull * T && v.depth < Dmax && x[v.s] < x[v.e - 1];
-    if (split) {
-      v.fanout = (uint32_t)((n + T - 1) / T);
-      v.scale = (double)v.fanout / (double)n;
-      if (route(v, x[v.s]) == route(v, x[v.e - 1])) split = false;
-    }
-    if (!split) {
-      make_leaf(v, S);
-      m.node[i] = v;
-      continue;
-    }
-    v.child0 = m.node.size();
-    std::vector<uint64_t> cs(v.fanout + 1, v.e);
-    uint64_t k = v.s;
-    for (uint32_t c = 0; c < v.fanout; ++c) {
-      while (k < v.e && route(v, x[k]) < c) ++k;
-      cs[c] = k;
-    }
-    m.node[i] = v;
-    for (uint32_t c = 0; c < v.fanout; ++c) {
-      Node ch;
-      ch.s = cs[c];
-      ch.e = cs[c + 1];
-      ch.depth = v.depth + 1;
-      m.node.push_back(ch);
-    }
+    lv0 = lv1;
+    lv1 = m.node.size();
   }
   return m;
 }
@@ -403,6 +423,27 @@ int eo_sort(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint32_t 
     for (uint32_t t = 0; t < B; ++t) bin_counts[t] = counts[t];
   if (cuts_out)
     for (uint32_t p = 0; p <= P; ++p) cuts_out[p] = c[p];
+  return 0;
+}
+
+// Partition step alone (for full-size checks): fine-bin counts and partition
+// offsets of all n records, without sorting.
+int eo_classify(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint32_t T, uint32_t Dmax, uint64_t S,
+                uint64_t seed, int balance, uint64_t* bin_counts, uint64_t* part_off) {
+  if (P < 1 || (P & (P - 1)) || log2B > 24 || (1u << log2B) < P || T < 1) return 1;
+  if (S >= (1ull << 24) || n == 0 || S == 0) return 1;
+  std::vector<uint64_t> sample(S);
+  eo_sample(in, n, S, seed, sample.data());
+  std::sort(sample.begin(), sample.end());
+  Rmi m = rmi_fit(sample.data(), S, T, Dmax);
+  uint32_t B = 1u << log2B;
+  std::vector<uint64_t> counts(B, 0);
+  for (uint64_t i = 0; i < n; ++i) counts[fine_bin(rmi_cdf(m, encode9(in + i * kRecord)), log2B)]++;
+  std::vector<uint32_t> c = cuts_of(counts, P, log2B, n, balance);
+  std::vector<uint64_t> C(B + 1, 0);
+  for (uint32_t t = 0; t < B; ++t) C[t + 1] = C[t] + counts[t];
+  for (uint32_t p = 0; p <= P; ++p) part_off[p] = C[c[p]];
+  for (uint32_t t = 0; t < B; ++t) bin_counts[t] = counts[t];
   return 0;
 }
 

@@ -76,7 +76,25 @@ def test_monotone_random_pairs_vs_memcmp(orc):
             assert enc[a] == enc[a + 1]
 
 
-def test_out_of_range_bytes_clamp(orc):
+def test_out_of_range_bytes_saturate(orc):
     assert orc.encode9(b"\x00" * 10) == 0
     assert orc.encode9(b"\xff" * 9 + b" ") == 95**9 - 1
-    assert orc.encode9(b"\x1f" + b"~" * 8 + b" ") < orc.encode9(b"!" + b" " * 9)
+    # after the first byte above 126 every digit is 94; after one below 32 every digit is 0
+    assert orc.encode9(b"\x7f" + b" " * 9) == 95**9 - 1
+    assert orc.encode9(b"A\x80" + b" " * 8) == 33 * 95**8 + 95**8 - 1
+    assert orc.encode9(b"A~\x01~~~~~~~") == 33 * 95**8 + 94 * 95**7
+    assert orc.encode9(b"\x1f" + b"~" * 9) == 0
+
+
+def test_monotone_on_arbitrary_bytes(orc):
+    """Eq. 1 needs the encoding monotone in memcmp order for every key, printable or not."""
+    rng = np.random.default_rng(3)
+    pool = np.array([0, 1, 31, 32, 33, 64, 125, 126, 127, 128, 200, 255], dtype=np.uint8)
+    keys = np.where(rng.random((20000, 10)) < 0.5, rng.choice(pool, size=(20000, 10)),
+                    rng.integers(0, 256, size=(20000, 10), dtype=np.uint8)).astype(np.uint8)
+    keys[1::2, :4] = keys[0::2, :4]  # shared prefixes
+    order = sorted(range(len(keys)), key=lambda i: bytes(keys[i]))
+    recs = np.zeros((len(keys), 100), dtype=np.uint8)
+    recs[:, :10] = keys[order]
+    enc = orc.encode9_records(recs.reshape(-1))
+    assert np.all(np.diff(enc.astype(np.float64)) >= 0) and np.all(enc[1:] >= enc[:-1])
