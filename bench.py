@@ -1,0 +1,320 @@
+"""Benchmark: GB/s sorted of 100-byte records on one B300 (or N replicas).
+
+Workload: 100M records x 100 B resident in HBM, two key sets -- uniform
+printable ASCII and Zipf(1.1) per key byte with a per-position permutation
+and 5 % exact duplicates -- 1024 partitions.  One step sorts both sets
+(2 x 10 GB) through the C ABI (elsar_sort).  value = bytes sorted / time.
+
+Also reported: the plain form (the paper's partition rule, one sort launch per
+partition) on the same data, the end-to-end rate through elsar_sort_host with
+pinned host buffers (copies inside the timed region), the roofline of the
+dominant kernel from live CUDA events, and the oracle timed on the host cores
+on a bounded sample of the same workload.
+
+python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_RECORDS = 100_000_000
+PARTITIONS = 1024
+RECORD = 100
+# algorithmic bytes per record of the sort+gather kernel: read the 16-byte
+# pair, read the 100-byte record, write it to its place in the output
+SORT_GATHER_BYTES = 16 + 100 + 100
+CPU_SAMPLE = 10_000_000  # records of each key set sorted by the oracle for the CPU baseline
+METRIC = "GB/s sorted (100-B recs), learned+batched vs plain on 1 B300; % HBM roofline"
+
+
+def workloads():
+    import recgen
+
+    return [recgen.UNIFORM_100M, recgen.ZIPF11_100M]
+
+
+def workload_config(extra=None):
+    cfg = {
+        "workload": "100M x 100-byte records in HBM, two key sets (uniform printable ASCII; Zipf s=1.1 per byte "
+                    "with per-position permutation and 5% duplicate keys), 1024 partitions, both sets sorted per step",
+        "n_records_per_set": N_RECORDS,
+        "sets": 2,
+        "partitions": PARTITIONS,
+        "cdf": "rmi",
+        "balance": "refined",
+        "schedule": "persistent",
+        "l2": "no flush needed: each input (10 GB) is far larger than L2 (126 MB)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6400.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 "--query-gpu=clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        load = [s for s in sm if s > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(args, world_rank=0):
+    """The oracle, as it stands, on a bounded sample of each key set (first CPU_SAMPLE records)."""
+    import oracle
+    import recgen
+
+    tot_bytes, tot_s = 0, 0.0
+    for wl in workloads():
+        host = recgen.generate_cpu(N_RECORDS, wl["spec"], i0=0, count=CPU_SAMPLE)
+        log2B = oracle.default_fine_log2(CPU_SAMPLE, PARTITIONS)
+        t0 = time.perf_counter()
+        oracle.sort(host, PARTITIONS, log2B, S=oracle.default_sample_size(CPU_SAMPLE), seed=0x5EED, balance=1)
+        tot_s += time.perf_counter() - t0
+        tot_bytes += CPU_SAMPLE * RECORD
+    return {"value": round(tot_bytes / tot_s / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {CPU_SAMPLE:,} records of each of the two 100M-record key sets, oracle sort "
+                      f"(1024 partitions, 1% sample), single-threaded"}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if args.impl == "elsar" else "gloo"
+        dist.init_process_group(backend)
+    return world, rank, local
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps would only repeat the same CPU work
+    t0 = time.perf_counter()
+    vals = [cpu_baseline(args) for _ in range(args.steps)]
+    dt = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(dt / args.steps * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": workload_config(),
+            "cpu_baseline": dict(vals[-1], value=round(v, 4)),
+            "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_elsar(args):
+    import torch
+
+    import paper_2305_05671_b300 as elsar
+    import recgen
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    p = elsar.Params(num_partitions=PARTITIONS, seed=0x5EED, tile_pairs=args.tile_pairs)
+    p_plain = elsar.Params(num_partitions=PARTITIONS, seed=0x5EED, balance=elsar.BALANCE_PAPER,
+                           schedule=elsar.SCHED_PER_PARTITION, tile_pairs=args.tile_pairs)
+    n = N_RECORDS
+    ins = []
+    for wl in workloads():
+        d = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
+        recgen.generate_gpu(d, n, wl["spec"], stream=stream.cuda_stream)
+        ins.append(d)
+    out = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
+    ws = elsar.alloc_workspace(n, p, device=dev)
+    torch.cuda.synchronize()
+
+    def step(params, stats=True):
+        sts = [elsar.sort(d, out, n, params, ws=ws, stream=stream, stats=stats) for d in ins]
+        return sts
+
+    for _ in range(args.warmup):
+        step(p)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    all_stats = []
+    with Clocks(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            all_stats.append(step(p))
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ms, world)
+    bytes_per_step = len(ins) * n * RECORD
+    value = world * bytes_per_step / (ms / 1e3) / 1e9
+
+    # the dominant kernel: sort + gather (pass 4), timed by the library's events on the launching stream
+    flat = [s for st in all_stats for s in st]
+    pass_ms = [statistics.mean(s["pass_ms"][k] for s in flat) for k in range(5)]
+    launches = int(sum(s["launches"] for s in flat) / args.steps)
+    peaks, how = measured_peaks()
+    sg_ms = pass_ms[4]
+    achieved = n * SORT_GATHER_BYTES / (sg_ms / 1e3) / 1e9
+    roof = {"kernel": "sort_gather_kernel", "bound": "hbm", "achieved": round(achieved, 1),
+            "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
+            "peak_source": how, "traffic": args.traffic,
+            "bytes_per_record": SORT_GATHER_BYTES, "avg_launch_ms": round(sg_ms, 3)}
+
+    # plain form on the same data
+    for _ in range(args.warmup):
+        step(p_plain, stats=False)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step(p_plain, stats=False)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1) / args.steps
+    plain = {"value": round(bytes_per_step / (plain_ms / 1e3) / 1e9, 2), "ms_per_step": round(plain_ms, 3),
+             "form": "paper partition rule, one sort launch per partition"}
+
+    # end to end through elsar_sort_host: pinned host in -> device -> sorted -> pinned host out
+    e2e = None
+    if not args.no_e2e:
+        h_ins = [d.cpu().pin_memory() for d in ins]
+        h_out = torch.empty(n * RECORD, dtype=torch.uint8).pin_memory()
+        del ins
+        torch.cuda.empty_cache()
+        d_in = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
+        elsar.sort_host(h_ins[0], h_out, n, p, d_in, out, ws, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for h in h_ins:
+                elsar.sort_host(h, h_out, n, p, d_in, out, ws, stream=stream)
+        torch.cuda.synchronize()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world)
+        e2e = {"value": round(world * bytes_per_step / e2e_s / 1e9, 3), "unit": "GB/s",
+               "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": bytes_per_step,
+               "steps": args.e2e_steps}
+    if rank != 0:
+        return
+    cpu = cpu_baseline(args) if world == 1 and not args.no_cpu else None
+    z = all_stats[-1]
+    line = {
+        "metric": METRIC,
+        "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic", "config": workload_config({"tile_pairs": args.tile_pairs or 4096}),
+        "records_per_s": round(world * len(workloads()) * n / (ms / 1e3)),
+        "hbm_frac_200B": round(world * len(workloads()) * n * 200 / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "plain": plain,
+        "passes_ms": {"fit": round(pass_ms[0], 3), "classify": round(pass_ms[1], 3),
+                      "scan_cuts_items": round(pass_ms[2], 3), "scatter": round(pass_ms[3], 3),
+                      "sort_gather": round(sg_ms, 3)},
+        "imbalance": {w["name"]: round(s["max_partition"] / (n / PARTITIONS), 4) for w, s in zip(workloads(), z)},
+        "oversize_items": [s["oversize_items"] for s in z],
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="elsar", choices=["elsar", "reference"])
+    ap.add_argument("--tile-pairs", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="ncu dram bytes per launch of the sort kernel (from the committed profile)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_elsar(args)
+
+
+if __name__ == "__main__":
+    main()

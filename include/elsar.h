@@ -1,0 +1,176 @@
+/*
+ * elsar.h -- C ABI of libelsar, a B300 (sm_103a) GPU implementation of the
+ * in-memory hot path of ELSAR, the learned partition-and-concatenate sort of
+ * "Parallel External Sorting of ASCII Records Using Learned Models"
+ * (arXiv 2305.05671).
+ *
+ * Records are fixed 100-byte ASCII records with a 10-byte key at offset 0
+ * (the paper's benchmark format, Sec. 7.1).  The result of every sort is the
+ * input records stably sorted by memcmp on the key (Sec. 7.1 methodology):
+ * equal keys stay in input order.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named d_* are device pointers (CUDA global memory) owned by the
+ *    caller; h_* are host pointers owned by the caller.  The library keeps no
+ *    reference to any buffer after a call returns.
+ *  - Record buffers must be 4-byte aligned; input and output must not
+ *    overlap.  Workspace and model buffers must be 256-byte aligned.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy
+ *    default stream) unless stated otherwise.  Some calls read a few bytes back
+ *    to the host (stated per call) and therefore synchronise `stream`.
+ *  - Errors are returned as an elsar_status; nothing is thrown and nothing
+ *    aborts.  elsar_last_error() gives a message for the calling thread.
+ *  - Supported: 0 <= n < 2^32 records.  Larger n returns ELSAR_EUNSUPPORTED.
+ *  - The library allocates no device memory: scratch lives in the caller's
+ *    workspace (size from elsar_workspace_size).
+ */
+#ifndef ELSAR_H
+#define ELSAR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ELSAR_RECORD_BYTES 100
+#define ELSAR_KEY_BYTES 10
+
+typedef struct CUstream_st* elsar_stream_t; /* same type as cudaStream_t */
+
+typedef enum elsar_status {
+  ELSAR_OK = 0,
+  ELSAR_EINVAL = 1,       /* bad argument (null/misaligned pointer, bad parameter) */
+  ELSAR_ENOMEM = 2,       /* a caller buffer (workspace, model) is too small */
+  ELSAR_ECUDA = 3,        /* a CUDA call failed; elsar_last_error() has the CUDA message */
+  ELSAR_ETIMEOUT = 4,     /* a device-side bounded wait gave up (reported in the status word) */
+  ELSAR_EUNSUPPORTED = 5, /* n >= 2^32 or another unsupported size */
+  ELSAR_EMODEL = 6        /* the model buffer does not hold a fitted model */
+} elsar_status;
+
+typedef enum elsar_model_kind {
+  ELSAR_MODEL_RMI = 0, /* the paper's RMI of linear models (Sec. 3.1) */
+  ELSAR_MODEL_MLP = 1  /* monotone MLP CDF trained on the GPU; the RMI is its fallback */
+} elsar_model_kind;
+
+typedef enum elsar_balance {
+  ELSAR_BALANCE_PAPER = 0,  /* partition p = min(P-1, floor(P * F(x)))  (Algorithm 1 reader loop) */
+  ELSAR_BALANCE_REFINED = 1 /* cuts at the fine-bin boundaries closest to p*N/P (exact counts) */
+} elsar_balance;
+
+typedef enum elsar_schedule {
+  ELSAR_SCHED_PER_PARTITION = 0, /* one sort launch per partition */
+  ELSAR_SCHED_PERSISTENT = 1     /* one persistent kernel over a work queue of all partitions */
+} elsar_schedule;
+
+/* Parameters.  Zero fields take the defaults noted; elsar_default_params
+ * fills them explicitly. */
+typedef struct elsar_params {
+  uint32_t num_partitions; /* P, power of two in [1, 65536]; default 1024 */
+  uint32_t fine_bins_log2; /* log2 B of the model's fine bins; 0 = about 1024 records per bin,
+                              clamped to [max(log2 P, 6), 20]; must be >= log2 P, <= 22 */
+  uint32_t leaf_target;    /* T: an RMI node splits when it holds more than 2T sample keys; 0 = 16 */
+  uint32_t max_depth;      /* RMI depth cap; 0 = 32 */
+  uint32_t model_kind;     /* elsar_model_kind; default RMI */
+  uint32_t balance;        /* elsar_balance; default REFINED */
+  uint32_t schedule;       /* elsar_schedule; default PERSISTENT */
+  uint32_t tile_pairs;     /* max pairs one CTA sorts in shared memory; 0 = tuned default */
+  uint64_t sample_size;    /* S; 0 = 1% of n within [1000, 10^7] (Sec. 3.1, Sec. 6); must be < 2^24 */
+  uint64_t seed;           /* seed of the key sample (SplitMix64 counter stream) */
+} elsar_params;
+
+/* Per-call measurements, filled when a non-NULL pointer is passed.  Passing
+ * one makes the call record CUDA events and synchronise `stream` at the end. */
+typedef struct elsar_stats {
+  float pass_ms[8];     /* 0 fit, 1 classify+histogram, 2 scan/cuts/items, 3 scatter, 4 sort+gather */
+  uint32_t launches;    /* kernels launched by the call */
+  uint32_t num_items;   /* work items of the sort pass */
+  uint32_t oversize_items;
+  uint32_t model_nodes; /* RMI nodes */
+  uint64_t max_partition;
+  uint64_t max_bin;
+} elsar_stats;
+
+/* Fill *p with the defaults. */
+void elsar_default_params(elsar_params* p);
+
+/* Bytes of workspace elsar_sort needs for n records with these parameters
+ * (elsar_fit_model, elsar_partition and elsar_sort_partitions need no more). */
+size_t elsar_workspace_size(uint64_t n, const elsar_params* p);
+
+/* Bytes of the device model buffer (fitted CDF model + fine-bin splitters). */
+size_t elsar_model_size(uint64_t n, const elsar_params* p);
+
+/*
+ * Train the CDF model (Sec. 3.1) on a uniform key sample of d_records:
+ * S sample positions mulhi64(SplitMix64_k(seed), n), their keys encoded in
+ * base 95 (Sec. 4), sorted, an RMI of linear models fitted on the sorted
+ * sample, then the B-1 fine-bin splitters of the model (the smallest key
+ * encoding whose fine bin floor(B*F) is at least q).  Writes d_model
+ * (elsar_model_size bytes).  Reads a few bytes back per RMI level, so it
+ * synchronises `stream`.
+ * Errors: EINVAL (null/misaligned pointers, bad params, n == 0), ENOMEM
+ * (buffers too small), EUNSUPPORTED (n >= 2^32), ECUDA.
+ */
+elsar_status elsar_fit_model(const void* d_records, uint64_t n, const elsar_params* p, void* d_model,
+                             size_t model_bytes, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
+
+/*
+ * Model-based partitioning (Sec. 3.3, Algorithm 1 reader loop, Eq. 1): for
+ * every record, the key is packed into a 16-byte pair {hi = big-endian key
+ * bytes 0-7; lo = (big-endian key bytes 8-9) << 32 | record index} and
+ * classified by the model into a fine bin q; bins are counted, scanned, the
+ * partitions cut (paper rule or refined rule) and the pairs scattered so that
+ * d_pairs holds them grouped by fine bin in bin order (hence by partition, and
+ * by model sub-bucket within each partition).
+ * Outputs: d_pairs (n * 16 bytes, 16-byte aligned), d_bin_offsets (B+1 u32:
+ * start of each fine bin in d_pairs), d_part_offsets (P+1 u64: start of each
+ * partition, Sec. 3.5 write offsets).  Order inside one bin is unspecified.
+ * Errors: EINVAL, ENOMEM, EMODEL (d_model not fitted for these params), ECUDA.
+ */
+elsar_status elsar_partition(const void* d_model, const void* d_records, uint64_t n, const elsar_params* p,
+                             void* d_pairs, uint32_t* d_bin_offsets, uint64_t* d_part_offsets, void* d_ws,
+                             size_t ws_bytes, elsar_stream_t stream);
+
+/*
+ * Sort every partition and concatenate (Sec. 3.4, Sec. 3.5): each fine bin of
+ * d_pairs (as laid out by elsar_partition) is sorted in shared memory by
+ * (key, record index), and the 100-byte records are gathered in that order
+ * into d_out (n * 100 bytes).  d_pairs is overwritten with the sorted pairs
+ * when a bin needs the multi-pass path; otherwise it is left as is.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+elsar_status elsar_sort_partitions(const void* d_records, uint64_t n, const elsar_params* p, void* d_pairs,
+                                   const uint32_t* d_bin_offsets, void* d_out, void* d_ws, size_t ws_bytes,
+                                   elsar_stream_t stream);
+
+/*
+ * The whole method on one record set resident in device memory:
+ * elsar_fit_model, elsar_partition and elsar_sort_partitions back to back,
+ * with their buffers carved from d_ws.  d_out receives the sorted records.
+ * Synchronises `stream` (model fitting reads back level sizes).
+ * Errors: as the three calls.
+ */
+elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_params* p, void* d_ws,
+                        size_t ws_bytes, elsar_stream_t stream, elsar_stats* stats);
+
+/*
+ * End-to-end convenience: host records in, host records out.  Copies
+ * h_in to d_in, sorts into d_out, copies d_out to h_out, all on `stream`
+ * (pinned host buffers make the copies asynchronous DMA).  Synchronises.
+ */
+elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_in,
+                             void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
+
+/* Static description of a status code. */
+const char* elsar_status_str(elsar_status s);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* elsar_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ELSAR_H */

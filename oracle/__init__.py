@@ -49,6 +49,7 @@ def lib():
             "eo_rmi_eval": (None, [I32, P, U64, P, P]),
             "eo_rmi_release": (None, []),
             "eo_sort": (I32, [P, U64, U32, U32, U32, U32, U64, U64, I32, P, P, P, P, P, P]),
+            "eo_classify": (I32, [P, U64, U32, U32, U32, U32, U64, U64, I32, P, P]),
             "eo_stable_sort": (None, [P, U64, P]),
             "eo_validate": (I32, [P, P, U64]),
         }
@@ -163,6 +164,18 @@ def sort(recs: np.ndarray, P: int, log2B: int, S: int, seed: int, balance: int =
     if want_detail:
         return out, dict(q=q, pid=pid, part_off=off, bin_counts=counts, cuts=cuts)
     return out
+
+
+def classify(recs: np.ndarray, P: int, log2B: int, S: int, seed: int, balance: int = 1, T: int = LEAF_TARGET,
+             Dmax: int = MAX_DEPTH):
+    """Fine-bin counts and partition offsets of every record (no sort)."""
+    n = recs.size // RECORD
+    counts = np.empty(1 << log2B, dtype=np.uint64)
+    off = np.empty(P + 1, dtype=np.uint64)
+    rc = lib().eo_classify(_ptr(recs), n, P, log2B, T, Dmax, S, seed, balance, _ptr(counts), _ptr(off))
+    if rc:
+        raise ValueError(f"eo_classify rc={rc}")
+    return counts, off
 
 
 def stable_sort(recs: np.ndarray) -> np.ndarray:

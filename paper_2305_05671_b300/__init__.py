@@ -1,0 +1,203 @@
+"""Python binding of libelsar (include/elsar.h): argument marshalling only.
+
+Every step of the sort runs in the CUDA kernels of libelsar.so; this module
+turns torch tensors into pointers, calls the C ABI and raises on errors.  It
+refuses to run when the library is missing -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass, fields
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libelsar.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "elsar.h")
+RECORD = 100
+
+MODEL_RMI, MODEL_MLP = 0, 1
+BALANCE_PAPER, BALANCE_REFINED = 0, 1
+SCHED_PER_PARTITION, SCHED_PERSISTENT = 0, 1
+
+
+class ElsarError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"elsar status {status}: {message}")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("num_partitions", ctypes.c_uint32), ("fine_bins_log2", ctypes.c_uint32),
+                ("leaf_target", ctypes.c_uint32), ("max_depth", ctypes.c_uint32), ("model_kind", ctypes.c_uint32),
+                ("balance", ctypes.c_uint32), ("schedule", ctypes.c_uint32), ("tile_pairs", ctypes.c_uint32),
+                ("sample_size", ctypes.c_uint64), ("seed", ctypes.c_uint64)]
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("pass_ms", ctypes.c_float * 8), ("launches", ctypes.c_uint32), ("num_items", ctypes.c_uint32),
+                ("oversize_items", ctypes.c_uint32), ("model_nodes", ctypes.c_uint32),
+                ("max_partition", ctypes.c_uint64), ("max_bin", ctypes.c_uint64)]
+
+
+@dataclass
+class Params:
+    """elsar_params; zero means "library default"."""
+
+    num_partitions: int = 1024
+    fine_bins_log2: int = 0
+    leaf_target: int = 16
+    max_depth: int = 32
+    model_kind: int = MODEL_RMI
+    balance: int = BALANCE_REFINED
+    schedule: int = SCHED_PERSISTENT
+    tile_pairs: int = 0
+    sample_size: int = 0
+    seed: int = 0x5EED
+
+    def c(self) -> _Params:
+        return _Params(*[getattr(self, f.name) for f in fields(self)])
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, U64, SZ = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t
+        PP = ctypes.POINTER(_Params)
+        sig = {
+            "elsar_default_params": (None, [PP]),
+            "elsar_workspace_size": (SZ, [U64, PP]),
+            "elsar_model_size": (SZ, [U64, PP]),
+            "elsar_fit_model": (ctypes.c_int, [P, U64, PP, P, SZ, P, SZ, P]),
+            "elsar_partition": (ctypes.c_int, [P, P, U64, PP, P, P, P, P, SZ, P]),
+            "elsar_sort_partitions": (ctypes.c_int, [P, U64, PP, P, P, P, P, SZ, P]),
+            "elsar_sort": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_Stats)]),
+            "elsar_sort_host": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
+            "elsar_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+            "elsar_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/elsar.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(elsar_[a-z_]+)\s*\(", txt)))
+
+
+def _check(rc: int):
+    if rc != 0:
+        L = lib()
+        raise ElsarError(rc, f"{L.elsar_status_str(rc).decode()}: {L.elsar_last_error().decode()}")
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    return t.ctypes.data  # numpy
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _nbytes(t) -> int:
+    return t.numel() * t.element_size() if hasattr(t, "numel") else t.nbytes
+
+
+def default_params() -> Params:
+    c = _Params()
+    lib().elsar_default_params(ctypes.byref(c))
+    return Params(*[getattr(c, f.name) for f in fields(Params)])
+
+
+def workspace_size(n: int, p: Params | None = None) -> int:
+    return int(lib().elsar_workspace_size(n, ctypes.byref((p or Params()).c())))
+
+
+def model_size(n: int, p: Params | None = None) -> int:
+    return int(lib().elsar_model_size(n, ctypes.byref((p or Params()).c())))
+
+
+def alloc_workspace(n: int, p: Params | None = None, device="cuda"):
+    import torch
+
+    return torch.empty(max(256, workspace_size(n, p)), dtype=torch.uint8, device=device)
+
+
+def fit_model(d_records, n: int, p: Params, d_model, ws, stream=None):
+    _check(lib().elsar_fit_model(_ptr(d_records), n, ctypes.byref(p.c()), _ptr(d_model), _nbytes(d_model), _ptr(ws),
+                                 _nbytes(ws), _stream(stream)))
+
+
+def partition(d_model, d_records, n: int, p: Params, d_pairs, d_bin_offsets, d_part_offsets, ws, stream=None):
+    _check(lib().elsar_partition(_ptr(d_model), _ptr(d_records), n, ctypes.byref(p.c()), _ptr(d_pairs),
+                                 _ptr(d_bin_offsets), _ptr(d_part_offsets), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def sort_partitions(d_records, n: int, p: Params, d_pairs, d_bin_offsets, d_out, ws, stream=None):
+    _check(lib().elsar_sort_partitions(_ptr(d_records), n, ctypes.byref(p.c()), _ptr(d_pairs), _ptr(d_bin_offsets),
+                                       _ptr(d_out), _ptr(ws), _nbytes(ws), _stream(stream)))
+
+
+def sort(d_in, d_out, n: int, p: Params | None = None, ws=None, stream=None, stats: bool = False):
+    """Sort n records of d_in into d_out (both CUDA uint8 tensors); returns a stats dict if asked."""
+    p = p or Params()
+    if ws is None:
+        ws = alloc_workspace(n, p, device=d_in.device)
+    st = _Stats() if stats else None
+    _check(lib().elsar_sort(_ptr(d_in), _ptr(d_out), n, ctypes.byref(p.c()), _ptr(ws), _nbytes(ws), _stream(stream),
+                            ctypes.byref(st) if st is not None else None))
+    if st is None:
+        return None
+    return dict(pass_ms=list(st.pass_ms)[:5], launches=st.launches, num_items=st.num_items,
+                oversize_items=st.oversize_items, model_nodes=st.model_nodes, max_partition=st.max_partition,
+                max_bin=st.max_bin)
+
+
+def sort_host(h_in, h_out, n: int, p: Params, d_in, d_out, ws, stream=None):
+    """Host records in (pinned for async DMA), host records out; synchronises."""
+    _check(lib().elsar_sort_host(_ptr(h_in), _ptr(h_out), n, ctypes.byref(p.c()), _ptr(d_in), _ptr(d_out), _ptr(ws),
+                                 _nbytes(ws), _stream(stream)))
+
+
+# ---- device model buffer layout (read back for inspection and parity tests)
+MODEL_HEADER_BYTES = 256
+NODE_BYTES = 64
+
+
+def read_model(d_model, p: Params, n: int):
+    """Host copy of a fitted model: (header dict, nodes structured array, splitters uint64)."""
+    import numpy as np
+
+    buf = d_model.cpu().numpy()
+    hdr = np.frombuffer(buf[:72].tobytes(), dtype=np.dtype([
+        ("magic", "<u4"), ("kind", "<u4"), ("log2B", "<u4"), ("num_nodes", "<u4"), ("S", "<u8"), ("node_cap", "<u8"),
+        ("nodes_off", "<u8"), ("splitters_off", "<u8"), ("bytes", "<u8"), ("T", "<u4"), ("Dmax", "<u4"),
+        ("levels", "<u4"), ("fallback", "<u4")]))[0]
+    ndt = np.dtype([("s", "<u4"), ("e", "<u4"), ("base", "<u8"), ("child0", "<u4"), ("fanout", "<u4"),
+                    ("shift", "<u4"), ("depth", "<u4"), ("a", "<f8"), ("b", "<f8"), ("c", "<f8"), ("h", "<f8")])
+    nn = int(hdr["num_nodes"])
+    off = int(hdr["nodes_off"])
+    nodes = np.frombuffer(buf[off:off + nn * NODE_BYTES].tobytes(), dtype=ndt)
+    so = int(hdr["splitters_off"])
+    spl = np.frombuffer(buf[so:so + 8 * (1 << int(hdr["log2B"]))].tobytes(), dtype=np.uint64)
+    return {k: hdr[k].item() for k in hdr.dtype.names}, nodes, spl

@@ -1,0 +1,425 @@
+// C ABI of libelsar (declared in include/elsar.h): argument checks, parameter
+// defaults, the workspace layout, and the order of the GPU passes.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/elsar.h"
+#include "common.cuh"
+
+namespace elsar {
+size_t sort_smem_bytes(uint32_t cap);
+}
+
+using namespace elsar;
+
+namespace {
+
+thread_local std::string g_err;
+
+elsar_status fail(elsar_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+elsar_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(ELSAR_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+struct Resolved {
+  uint32_t P, log2B, T, Dmax, kind, balance, schedule, cap;
+  uint64_t S, seed;
+};
+
+uint32_t ilog2(uint64_t v) {
+  uint32_t r = 0;
+  while ((1ull << (r + 1)) <= v) ++r;
+  return r;
+}
+
+bool pow2(uint64_t v) { return v && !(v & (v - 1)); }
+
+elsar_status resolve(uint64_t n, const elsar_params* p, Resolved* r) {
+  elsar_params d;
+  elsar_default_params(&d);
+  const elsar_params& q = p ? *p : d;
+  r->P = q.num_partitions ? q.num_partitions : d.num_partitions;
+  if (!pow2(r->P) || r->P > 65536) return fail(ELSAR_EINVAL, "num_partitions must be a power of two <= 65536");
+  const uint32_t lp = ilog2(r->P);
+  if (q.fine_bins_log2) {
+    r->log2B = q.fine_bins_log2;
+  } else {
+    uint32_t want = 0;
+    while (want < 63 && (1ull << want) < (n ? n : 1)) ++want;  // ceil(log2 n)
+    want = want > 10 ? want - 10 : 0;
+    uint32_t b = want < 6 ? 6 : want;
+    if (b > 20) b = 20;
+    r->log2B = b > lp ? b : lp;
+  }
+  if (r->log2B < lp || r->log2B > 22) return fail(ELSAR_EINVAL, "fine_bins_log2 must be in [log2 P, 22]");
+  r->T = q.leaf_target ? q.leaf_target : 16;
+  r->Dmax = q.max_depth ? q.max_depth : 32;
+  r->kind = q.model_kind;
+  if (r->kind > 1) return fail(ELSAR_EINVAL, "unknown model_kind");
+  r->balance = q.balance;
+  if (r->balance > 1) return fail(ELSAR_EINVAL, "unknown balance rule");
+  r->schedule = q.schedule;
+  if (r->schedule > 1) return fail(ELSAR_EINVAL, "unknown schedule");
+  r->cap = q.tile_pairs ? q.tile_pairs : 4096;
+  if (!pow2(r->cap) || r->cap < 256 || r->cap > 8192) return fail(ELSAR_EINVAL, "tile_pairs must be a power of two in [256, 8192]");
+  if (q.sample_size) {
+    r->S = q.sample_size;
+  } else {
+    uint64_t s = (n + 99) / 100;
+    if (s < 1000) s = 1000;
+    if (s > 10000000) s = 10000000;
+    r->S = n ? s : 0;
+  }
+  if (r->S >= (1ull << 24)) return fail(ELSAR_EINVAL, "sample_size must be < 2^24");
+  r->seed = q.seed;
+  return ELSAR_OK;
+}
+
+struct Layout {
+  size_t ctrl, model, pairsA, pairsB, bin_off, part_off, cuts, cursor, items, item_flag, oversize, samp, pnode, sums,
+      fc, total;
+};
+
+size_t up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+Layout layout(uint64_t n, const Resolved& r) {
+  Layout L;
+  const uint64_t B = 1ull << r.log2B;
+  const uint64_t cap = node_cap_for(r.S, r.T);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += up(bytes);
+    return at;
+  };
+  L.ctrl = take((64 + 65537) * 4);
+  L.model = take(model_bytes_for(r.S, r.log2B, r.T));
+  L.pairsA = take(n * 16);
+  L.pairsB = take(n * 16);
+  L.bin_off = take((B + 1) * 4);
+  L.part_off = take((r.P + 1) * 8);
+  L.cuts = take((r.P + 1) * 4);
+  L.cursor = take(B * 4);
+  L.items = take((B + 1) * 4);
+  L.item_flag = take(B * 4);
+  L.oversize = take(B * 4);
+  L.samp = take(2 * r.S * 8);
+  L.pnode = take(r.S * 4);
+  L.sums = take(cap * 48);
+  L.fc = take(cap * 4);
+  L.total = o;
+  return L;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+template <typename T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<uint8_t*>(base) + off);
+}
+
+elsar_status common_checks(uint64_t n, const void* d_ws, size_t ws_bytes, const Layout& L) {
+  if (n >= (1ull << 32)) return fail(ELSAR_EUNSUPPORTED, "n must be < 2^32");
+  if (!d_ws || !aligned(d_ws, 256)) return fail(ELSAR_EINVAL, "workspace must be non-null and 256-byte aligned");
+  if (ws_bytes < L.total) return fail(ELSAR_ENOMEM, "workspace too small: %zu < %zu bytes", ws_bytes, L.total);
+  return ELSAR_OK;
+}
+
+const uint64_t* splitters_in(const void* d_model, const Resolved& r) {
+  return reinterpret_cast<const uint64_t*>(static_cast<const uint8_t*>(d_model) + 256 +
+                                           node_cap_for(r.S, r.T) * sizeof(DNode));
+}
+
+elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* d_model, void* d_ws, const Layout& L,
+                    cudaStream_t st, uint32_t* launches, uint32_t* nodes) {
+  FitArgs f = {};
+  f.records = static_cast<const uint8_t*>(d_records);
+  f.n = n;
+  f.S = r.S;
+  f.seed = r.seed;
+  f.log2B = r.log2B;
+  f.T = r.T;
+  f.Dmax = r.Dmax;
+  f.model = d_model;
+  f.model_bytes = model_bytes_for(r.S, r.log2B, r.T);
+  f.samp = at<uint64_t>(d_ws, L.samp);
+  f.pnode = at<uint32_t>(d_ws, L.pnode);
+  f.sums = at<uint64_t>(d_ws, L.sums);
+  f.fc = at<uint32_t>(d_ws, L.fc);
+  f.ctrl = at<uint32_t>(d_ws, L.ctrl);
+  f.stream = st;
+  f.launches = launches;
+  cudaError_t e = fit_rmi(f, nodes);
+  if (e != cudaSuccess) return cuda_fail(e, "fit");
+  return ELSAR_OK;
+}
+
+PartArgs part_args(const void* d_model, const void* d_records, uint64_t n, const Resolved& r, void* d_pairs,
+                   uint32_t* d_bin_off, uint64_t* d_part_off, void* d_ws, const Layout& L, cudaStream_t st,
+                   uint32_t* launches) {
+  PartArgs a = {};
+  a.records = static_cast<const uint8_t*>(d_records);
+  a.n = n;
+  a.splitters = splitters_in(d_model, r);
+  a.log2B = r.log2B;
+  a.P = r.P;
+  a.balance = r.balance;
+  a.tile_pairs = r.cap;
+  a.pairs_in_order = at<void>(d_ws, L.pairsA);
+  a.pairs = d_pairs;
+  a.bin_off = d_bin_off;
+  a.part_off = d_part_off;
+  a.cuts = at<uint32_t>(d_ws, L.cuts);
+  a.cursor = at<uint32_t>(d_ws, L.cursor);
+  a.items = at<uint32_t>(d_ws, L.items);
+  a.item_flag = at<uint32_t>(d_ws, L.item_flag);
+  a.oversize = at<uint32_t>(d_ws, L.oversize);
+  a.ctrl = at<uint32_t>(d_ws, L.ctrl);
+  a.stream = st;
+  a.launches = launches;
+  return a;
+}
+
+elsar_status do_sort_partitions(const void* d_records, uint64_t n, const Resolved& r, void* d_pairs,
+                                const uint32_t* d_bin_off, void* d_out, void* d_ws, const Layout& L, cudaStream_t st,
+                                uint32_t* launches, cudaEvent_t ev_items) {
+  PartArgs a = part_args(nullptr, d_records, n, r, d_pairs, const_cast<uint32_t*>(d_bin_off),
+                         at<uint64_t>(d_ws, L.part_off), d_ws, L, st, launches);
+  cudaError_t e = build_items(a);
+  if (e != cudaSuccess) return cuda_fail(e, "items");
+  if (ev_items) cudaEventRecord(ev_items, st);
+  SortArgs s = {};
+  s.records = static_cast<const uint8_t*>(d_records);
+  s.out = static_cast<uint8_t*>(d_out);
+  s.n = n;
+  s.log2B = r.log2B;
+  s.P = r.P;
+  s.schedule = r.schedule;
+  s.tile_pairs = r.cap;
+  s.pairs = static_cast<Pair*>(d_pairs);
+  s.temp = at<Pair>(d_ws, L.pairsA);
+  s.bin_off = d_bin_off;
+  s.items = a.items;
+  s.oversize = a.oversize;
+  s.cuts = a.cuts;
+  s.item_of_bin = a.item_flag;
+  s.ctrl = a.ctrl;
+  s.stream = st;
+  s.launches = launches;
+  e = sort_items(s);
+  if (e != cudaSuccess) return cuda_fail(e, "sort");
+  return ELSAR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void elsar_default_params(elsar_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->num_partitions = 1024;
+  p->fine_bins_log2 = 0;
+  p->leaf_target = 16;
+  p->max_depth = 32;
+  p->model_kind = ELSAR_MODEL_RMI;
+  p->balance = ELSAR_BALANCE_REFINED;
+  p->schedule = ELSAR_SCHED_PERSISTENT;
+  p->tile_pairs = 0;
+  p->sample_size = 0;
+  p->seed = 0x5EEDull;
+}
+
+size_t elsar_workspace_size(uint64_t n, const elsar_params* p) {
+  Resolved r;
+  if (resolve(n, p, &r) != ELSAR_OK) return 0;
+  return layout(n, r).total;
+}
+
+size_t elsar_model_size(uint64_t n, const elsar_params* p) {
+  Resolved r;
+  if (resolve(n, p, &r) != ELSAR_OK) return 0;
+  return model_bytes_for(r.S, r.log2B, r.T);
+}
+
+elsar_status elsar_fit_model(const void* d_records, uint64_t n, const elsar_params* p, void* d_model,
+                             size_t model_bytes, void* d_ws, size_t ws_bytes, elsar_stream_t stream) {
+  g_err.clear();
+  Resolved r;
+  elsar_status s = resolve(n, p, &r);
+  if (s != ELSAR_OK) return s;
+  if (n == 0) return fail(ELSAR_EINVAL, "cannot fit a model on 0 records");
+  const Layout L = layout(n, r);
+  if ((s = common_checks(n, d_ws, ws_bytes, L)) != ELSAR_OK) return s;
+  if (!d_records || !aligned(d_records, 4)) return fail(ELSAR_EINVAL, "records must be non-null and 4-byte aligned");
+  if (!d_model || !aligned(d_model, 256)) return fail(ELSAR_EINVAL, "model buffer must be 256-byte aligned");
+  if (model_bytes < model_bytes_for(r.S, r.log2B, r.T)) return fail(ELSAR_ENOMEM, "model buffer too small");
+  if (r.kind != ELSAR_MODEL_RMI) return fail(ELSAR_EUNSUPPORTED, "model_kind MLP is not available in this build");
+  uint32_t launches = 0, nodes = 0;
+  return do_fit(d_records, n, r, d_model, d_ws, L, (cudaStream_t)stream, &launches, &nodes);
+}
+
+elsar_status elsar_partition(const void* d_model, const void* d_records, uint64_t n, const elsar_params* p,
+                             void* d_pairs, uint32_t* d_bin_offsets, uint64_t* d_part_offsets, void* d_ws,
+                             size_t ws_bytes, elsar_stream_t stream) {
+  g_err.clear();
+  Resolved r;
+  elsar_status s = resolve(n, p, &r);
+  if (s != ELSAR_OK) return s;
+  const Layout L = layout(n, r);
+  if ((s = common_checks(n, d_ws, ws_bytes, L)) != ELSAR_OK) return s;
+  if (!d_model || !aligned(d_model, 256)) return fail(ELSAR_EINVAL, "model buffer must be 256-byte aligned");
+  if ((n && (!d_records || !aligned(d_records, 4))) || (n && (!d_pairs || !aligned(d_pairs, 16))) || !d_bin_offsets ||
+      !d_part_offsets)
+    return fail(ELSAR_EINVAL, "null or misaligned buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  ModelHeader h;
+  cudaError_t e = cudaMemcpyAsync(&h, d_model, sizeof(h), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "model header");
+  if (h.magic != kModelMagic || h.log2B != r.log2B || h.S != r.S || h.T != r.T)
+    return fail(ELSAR_EMODEL, "model buffer does not hold a model fitted with these parameters");
+  uint32_t launches = 0;
+  PartArgs a = part_args(d_model, d_records, n, r, d_pairs, d_bin_offsets, d_part_offsets, d_ws, L, st, &launches);
+  e = partition_records(a);
+  if (e != cudaSuccess) return cuda_fail(e, "partition");
+  return ELSAR_OK;
+}
+
+elsar_status elsar_sort_partitions(const void* d_records, uint64_t n, const elsar_params* p, void* d_pairs,
+                                   const uint32_t* d_bin_offsets, void* d_out, void* d_ws, size_t ws_bytes,
+                                   elsar_stream_t stream) {
+  g_err.clear();
+  Resolved r;
+  elsar_status s = resolve(n, p, &r);
+  if (s != ELSAR_OK) return s;
+  const Layout L = layout(n, r);
+  if ((s = common_checks(n, d_ws, ws_bytes, L)) != ELSAR_OK) return s;
+  if (n == 0) return ELSAR_OK;
+  if (!d_records || !aligned(d_records, 4) || !d_out || !aligned(d_out, 4) || !d_pairs || !aligned(d_pairs, 16) ||
+      !d_bin_offsets)
+    return fail(ELSAR_EINVAL, "null or misaligned buffer");
+  uint32_t launches = 0;
+  return do_sort_partitions(d_records, n, r, d_pairs, d_bin_offsets, d_out, d_ws, L, (cudaStream_t)stream, &launches,
+                            nullptr);
+}
+
+elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_params* p, void* d_ws, size_t ws_bytes,
+                        elsar_stream_t stream, elsar_stats* stats) {
+  g_err.clear();
+  Resolved r;
+  elsar_status s = resolve(n, p, &r);
+  if (s != ELSAR_OK) return s;
+  const Layout L = layout(n, r);
+  if ((s = common_checks(n, d_ws, ws_bytes, L)) != ELSAR_OK) return s;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n == 0) return ELSAR_OK;
+  if (!d_in || !aligned(d_in, 4) || !d_out || !aligned(d_out, 4)) return fail(ELSAR_EINVAL, "null or misaligned records");
+  const uint8_t* i8 = static_cast<const uint8_t*>(d_in);
+  const uint8_t* o8 = static_cast<const uint8_t*>(d_out);
+  if (i8 < o8 + n * ELSAR_RECORD_BYTES && o8 < i8 + n * ELSAR_RECORD_BYTES)
+    return fail(ELSAR_EINVAL, "input and output records overlap");
+  if (r.kind != ELSAR_MODEL_RMI) return fail(ELSAR_EUNSUPPORTED, "model_kind MLP is not available in this build");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t ev[7] = {};
+  if (stats)
+    for (auto& e : ev) cudaEventCreate(&e);
+  if (ev[0]) cudaEventRecord(ev[0], st);
+  uint32_t launches = 0, nodes = 0;
+  void* model = at<void>(d_ws, L.model);
+  s = do_fit(d_in, n, r, model, d_ws, L, st, &launches, &nodes);
+  if (s == ELSAR_OK) {
+    if (ev[1]) cudaEventRecord(ev[1], st);
+    PartArgs a = part_args(model, d_in, n, r, at<void>(d_ws, L.pairsB), at<uint32_t>(d_ws, L.bin_off),
+                           at<uint64_t>(d_ws, L.part_off), d_ws, L, st, &launches);
+    a.ev[0] = ev[2];
+    a.ev[1] = ev[3];
+    a.ev[2] = ev[4];
+    cudaError_t e = partition_records(a);
+    if (e != cudaSuccess) s = cuda_fail(e, "partition");
+  }
+  if (s == ELSAR_OK)
+    s = do_sort_partitions(d_in, n, r, at<void>(d_ws, L.pairsB), at<uint32_t>(d_ws, L.bin_off), d_out, d_ws, L, st,
+                           &launches, ev[5]);
+  if (s == ELSAR_OK && stats) {
+    cudaEventRecord(ev[6], st);
+    cudaError_t e = cudaEventSynchronize(ev[6]);
+    if (e != cudaSuccess) {
+      s = cuda_fail(e, "sort");
+    } else {
+      auto ms = [&](int a, int b) {
+        float t = 0;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+      };
+      stats->pass_ms[0] = ms(0, 1);
+      stats->pass_ms[1] = ms(1, 2);
+      stats->pass_ms[2] = ms(2, 3) + ms(4, 5);
+      stats->pass_ms[3] = ms(3, 4);
+      stats->pass_ms[4] = ms(5, 6);
+      stats->launches = launches;
+      stats->model_nodes = nodes;
+      uint32_t c[4];
+      cudaMemcpy(c, at<uint32_t>(d_ws, L.ctrl), sizeof c, cudaMemcpyDeviceToHost);
+      stats->num_items = c[kNumItems];
+      stats->oversize_items = c[kNumOversize];
+      stats->max_bin = c[kMaxBin];
+      std::string po((r.P + 1) * 8, '\0');
+      cudaMemcpy(&po[0], at<uint64_t>(d_ws, L.part_off), po.size(), cudaMemcpyDeviceToHost);
+      const uint64_t* off = reinterpret_cast<const uint64_t*>(po.data());
+      for (uint32_t q = 0; q < r.P; ++q)
+        if (off[q + 1] - off[q] > stats->max_partition) stats->max_partition = off[q + 1] - off[q];
+    }
+  }
+  if (stats)
+    for (auto& e : ev) cudaEventDestroy(e);
+  if (s == ELSAR_OK) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) s = cuda_fail(e, "launch");
+  }
+  return s;
+}
+
+elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_in,
+                             void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream) {
+  g_err.clear();
+  if (n && (!h_in || !h_out)) return fail(ELSAR_EINVAL, "null host buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = n * ELSAR_RECORD_BYTES;
+  cudaError_t e = n ? cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "copy in");
+  elsar_status s = elsar_sort(d_in, d_out, n, p, d_ws, ws_bytes, stream, nullptr);
+  if (s != ELSAR_OK) return s;
+  if (n && (e = cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "copy out");
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
+  return ELSAR_OK;
+}
+
+const char* elsar_status_str(elsar_status s) {
+  switch (s) {
+    case ELSAR_OK: return "ok";
+    case ELSAR_EINVAL: return "invalid argument";
+    case ELSAR_ENOMEM: return "buffer too small";
+    case ELSAR_ECUDA: return "CUDA error";
+    case ELSAR_ETIMEOUT: return "device wait timed out";
+    case ELSAR_EUNSUPPORTED: return "unsupported size or feature";
+    case ELSAR_EMODEL: return "model not fitted";
+  }
+  return "unknown status";
+}
+
+const char* elsar_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Internal declarations shared by the libelsar CUDA sources (not part of the ABI).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace elsar {
+
+constexpr int kRecord = 100;
+constexpr uint64_t kEncTop = 630249409724609375ull;  // 95^9: one past the largest 9-character encoding
+constexpr uint32_t kModelMagic = 0x52534C45u;        // "ELSR"
+constexpr uint32_t kSettled = 0xFFFFFFFFu;           // sample point whose RMI node is already a leaf
+constexpr int kCoarse = 4096;                        // splitter entries kept in shared memory for classification
+
+// 16-byte sort pair (the paper's pointer-only record, Sec. 3.3): ordering by
+// (hi, lo) is memcmp order of the 10-byte key, then input order.
+//   hi = key bytes 0-7 big-endian
+//   lo = (key bytes 8-9 big-endian) << 32 | record index
+struct __align__(16) Pair {
+  uint64_t hi;
+  uint64_t lo;
+};
+
+__device__ __forceinline__ bool pair_less(const Pair& a, const Pair& b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+
+// One RMI node (64 bytes).  Internal: a = gamma, b = delta, c = scale.
+// Leaf: a = g, b = d, c = lo, h = hi (output constants of Sec. 3.1's model).
+struct __align__(64) DNode {
+  uint32_t s, e;  // sample ranks covered
+  uint64_t base;
+  uint32_t child0, fanout;  // fanout 0 = leaf
+  uint32_t shift, depth;
+  double a, b, c, h;
+};
+
+struct ModelHeader {
+  uint32_t magic, kind, log2B, num_nodes;
+  uint64_t S, node_cap;
+  uint64_t nodes_off, splitters_off, bytes;
+  uint32_t T, Dmax, levels, fallback;
+};
+
+// Key encoding (Sec. 4): 9 base-95 digits (ASCII - 32) of printable bytes.
+// w0 = bytes 0-3, w1 = bytes 4-7 as big-endian words; b8 = byte 8.  A byte
+// outside 32..126 saturates that digit and every later one to 0 (below) or
+// 94 (above), which keeps the encoding monotone in byte order for any key.
+__device__ __forceinline__ uint32_t digits4(uint32_t w) {
+  w = __vsub4(w, 0x20202020u);
+  return (((w >> 24) * 95u + ((w >> 16) & 0xFFu)) * 95u + ((w >> 8) & 0xFFu)) * 95u + (w & 0xFFu);
+}
+
+static __device__ __noinline__ uint64_t enc9_saturating(uint32_t w0, uint32_t w1, uint32_t b8) {
+  uint64_t e = 0;
+  int sat = 0;
+  for (int i = 0; i < 9; ++i) {
+    uint32_t c = i < 4 ? (w0 >> (24 - 8 * i)) & 0xFFu : (i < 8 ? (w1 >> (56 - 8 * i)) & 0xFFu : b8);
+    if (sat == 0 && c < 32u) sat = 1;
+    if (sat == 0 && c > 126u) sat = 2;
+    e = e * 95u + (sat == 1 ? 0u : (sat == 2 ? 94u : c - 32u));
+  }
+  return e;
+}
+
+__device__ __forceinline__ uint64_t enc9_words(uint32_t w0, uint32_t w1, uint32_t b8) {
+  const uint32_t out = __vcmpltu4(w0, 0x20202020u) | __vcmpgtu4(w0, 0x7E7E7E7Eu) | __vcmpltu4(w1, 0x20202020u) |
+                       __vcmpgtu4(w1, 0x7E7E7E7Eu);
+  if (out | (b8 < 32u) | (b8 > 126u)) return enc9_saturating(w0, w1, b8);
+  return ((uint64_t)digits4(w0) * 81450625ull + digits4(w1)) * 95ull + (b8 - 32u);  // 95^4 = 81450625
+}
+
+__device__ __forceinline__ uint64_t enc9_pair(const Pair& p) {
+  return enc9_words((uint32_t)(p.hi >> 32), (uint32_t)p.hi, (uint32_t)(p.lo >> 40) & 0xFFu);
+}
+
+// Load the 10-byte key of a 4-byte-aligned record and pack it.
+__device__ __forceinline__ Pair load_pair(const uint8_t* rec, uint32_t idx) {
+  const uint32_t* w = reinterpret_cast<const uint32_t*>(rec);
+  uint32_t a = __ldg(w), b = __ldg(w + 1), c = __ldg(w + 2);
+  uint32_t be0 = __byte_perm(a, 0, 0x0123), be1 = __byte_perm(b, 0, 0x0123);
+  uint32_t be16 = __byte_perm(c, 0, 0x4401);
+  Pair p;
+  p.hi = ((uint64_t)be0 << 32) | be1;
+  p.lo = ((uint64_t)be16 << 32) | idx;
+  return p;
+}
+
+// Fine bin of a key encoding from the splitters t[0..B) (t[0] = 0):
+// q = largest j with t[j] <= x.  ct = every G-th splitter in shared memory.
+__device__ __forceinline__ uint32_t fine_bin(const uint64_t* __restrict__ t, const uint64_t* ct, uint32_t ncoarse,
+                                             uint32_t G, uint64_t x) {
+  uint32_t pos = 0;
+  for (uint32_t step = ncoarse >> 1; step; step >>= 1)
+    if (ct[pos + step] <= x) pos += step;
+  pos *= G;
+  for (uint32_t step = G >> 1; step; step >>= 1)
+    if (__ldg(t + pos + step) <= x) pos += step;
+  return pos;
+}
+
+// ---------------------------------------------------------------- launchers
+struct FitArgs {
+  const uint8_t* records;
+  uint64_t n, S, seed;
+  uint32_t log2B, T, Dmax;
+  void* model;
+  size_t model_bytes;
+  // scratch
+  uint64_t* samp;   // 2*S
+  uint32_t* pnode;  // S
+  uint64_t* sums;   // node_cap * 6
+  uint32_t* fc;     // node_cap
+  uint32_t* ctrl;   // 64 words
+  cudaStream_t stream;
+  uint32_t* launches;
+};
+
+size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T);
+uint64_t node_cap_for(uint64_t S, uint32_t T);
+cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out);
+
+struct PartArgs {
+  const uint8_t* records;
+  uint64_t n;
+  const uint64_t* splitters;  // B fine-bin splitters of the fitted model
+  uint32_t log2B, P, balance, tile_pairs;
+  void* pairs_in_order;  // n pairs (scratch)
+  void* pairs;           // n pairs, bin-ordered (output)
+  uint32_t* bin_off;     // B+1
+  uint64_t* part_off;    // P+1
+  uint32_t* cuts;        // P+1
+  uint32_t* cursor;      // B
+  uint32_t* items;       // B+1 : first bin of each item
+  uint32_t* item_flag;   // B   scratch (becomes the item id of every bin)
+  uint32_t* oversize;    // B   item ids of oversize items
+  uint32_t* ctrl;        // control words
+  cudaStream_t stream;
+  uint32_t* launches;
+  cudaEvent_t ev[4];  // optional: after classify, after scan/cuts/items, after scatter
+};
+
+cudaError_t partition_records(const PartArgs& a);
+cudaError_t build_items(const PartArgs& a);
+
+struct SortArgs {
+  const uint8_t* records;
+  uint8_t* out;
+  uint64_t n;
+  uint32_t log2B, P, schedule, tile_pairs;
+  Pair* pairs;  // bin-ordered
+  Pair* temp;   // n pairs scratch (oversize merges)
+  const uint32_t* bin_off;
+  const uint32_t* items;
+  const uint32_t* oversize;
+  const uint32_t* cuts;
+  const uint32_t* item_of_bin;
+  uint32_t* ctrl;  // control words; words [64, 64+P+1) hold per-partition item ranges
+  cudaStream_t stream;
+  uint32_t* launches;
+};
+
+cudaError_t sort_items(const SortArgs& a);
+int sm_count();
+
+// control word indices
+enum Ctrl : int {
+  kNumItems = 0,
+  kNumOversize = 1,
+  kQueueHead = 2,
+  kMaxBin = 3,
+  kStatus = 4,
+  kLevelNodes = 8,  // fit: [8] level begin, [9] level end, [10] next level count, [11] total nodes
+  kOversizeHead = 12,
+  kItemsCapped = 13,
+};
+
+}  // namespace elsar

@@ -1,0 +1,518 @@
+// Model training on the GPU (Sec. 3.1 of the paper): key sample, sample sort,
+// the RMI of linear models, and the fine-bin splitters classification uses.
+//
+// Every floating-point step uses explicit round-to-nearest intrinsics in the
+// order the model definition fixes (this file is also built with
+// -fmad=false), so the fitted model is bit-identical wherever it is computed
+// in that order.  Least-squares sums are exact integers (order independent).
+#include "common.cuh"
+
+namespace elsar {
+namespace {
+
+inline uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
+
+typedef unsigned __int128 u128;
+typedef __int128 i128;
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Correctly rounded (to nearest even) unsigned 128-bit -> double: keep the
+// top 64 bits with the discarded bits ORed into bit 0 (a sticky bit below
+// the rounding position), let the hardware round 64 -> 53 bits, then scale
+// by the exact power of two.
+__device__ __forceinline__ double u128_to_double(u128 v) {
+  uint64_t hi = (uint64_t)(v >> 64), lo = (uint64_t)v;
+  if (hi == 0) return __ull2double_rn(lo);
+  int s = 64 - __clzll((long long)hi);  // bits beyond the top 64: 1..64
+  uint64_t top = (uint64_t)(v >> s);
+  uint64_t sticky = (s == 64) ? (lo != 0) : ((lo & ((1ull << s) - 1)) != 0);
+  double d = __ull2double_rn(top | sticky);
+  return __dmul_rn(d, __longlong_as_double((long long)(1023 + s) << 52));
+}
+
+__device__ __forceinline__ double i128_to_double(i128 v) {
+  return v < 0 ? -u128_to_double((u128)(-v)) : u128_to_double((u128)v);
+}
+
+__device__ __forceinline__ double pos_or_zero(double v) { return v > 0.0 ? v : 0.0; }
+
+__device__ __forceinline__ uint64_t local_u(const DNode& v, uint64_t x) {
+  return x > v.base ? (x - v.base) >> v.shift : 0;
+}
+
+// router of an internal node: clamp(floor(fma(gamma, u, delta) * scale), 0, f-1)
+__device__ __forceinline__ uint32_t route(const DNode& v, uint64_t x) {
+  double t = __dmul_rn(__fma_rn(v.a, __ull2double_rn(local_u(v, x)), v.b), v.c);
+  if (!(t > 0.0)) return 0;
+  if (t >= __uint2double_rn(v.fanout)) return v.fanout - 1;
+  return __double2uint_rz(t);
+}
+
+__device__ __forceinline__ double model_cdf(const DNode* __restrict__ nodes, uint64_t x) {
+  uint32_t i = 0;
+  DNode v = nodes[0];
+  while (v.fanout) {
+    i = v.child0 + route(v, x);
+    v = nodes[i];
+  }
+  double y = __fma_rn(v.a, __ull2double_rn(local_u(v, x)), v.b);
+  if (y < v.c) return v.c;
+  if (y > v.h) return v.h;
+  return y;
+}
+
+__device__ __forceinline__ uint32_t model_bin(const DNode* __restrict__ nodes, uint64_t x, uint32_t log2B) {
+  uint32_t B = 1u << log2B;
+  uint32_t q = __double2uint_rz(__dmul_rn(model_cdf(nodes, x), __uint2double_rn(B)));
+  return q < B ? q : B - 1;
+}
+
+__device__ __forceinline__ void atomic_add_u128(uint64_t* p, u128 v) {
+  uint64_t lo = (uint64_t)v, hi = (uint64_t)(v >> 64);
+  unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)lo);
+  if (old + lo < old) hi += 1;
+  if (hi) atomicAdd(reinterpret_cast<unsigned long long*>(p + 1), (unsigned long long)hi);
+}
+
+__device__ __forceinline__ u128 shfl_down_u128(u128 v, int d) {
+  uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)v, d);
+  uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+  return ((u128)hi << 64) | lo;
+}
+
+// ------------------------------------------------------------------ sample
+__global__ void sample_kernel(const uint8_t* __restrict__ rec, uint64_t n, uint64_t S, uint64_t seed,
+                              uint64_t* __restrict__ out) {
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < S; k += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t i = __umul64hi(splitmix64_at(seed, k), n);
+    out[k] = enc9_pair(load_pair(rec + i * kRecord, 0));
+  }
+}
+
+// ------------------------------------------------------------------ u64 sort: chunk bitonic + merge path
+constexpr int kChunk = 4096;
+constexpr int kChunkThreads = 1024;
+
+__global__ void __launch_bounds__(kChunkThreads) chunk_sort_u64(uint64_t* data, uint64_t S) {
+  __shared__ uint64_t s[kChunk];
+  const uint64_t base = (uint64_t)blockIdx.x * kChunk;
+  for (int i = threadIdx.x; i < kChunk; i += kChunkThreads) s[i] = base + i < S ? data[base + i] : ~0ull;
+  __syncthreads();
+  for (int k = 2; k <= kChunk; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < kChunk; i += kChunkThreads) {
+        int ixj = i ^ j;
+        if (ixj > i) {
+          uint64_t a = s[i], b = s[ixj];
+          bool up = (i & k) == 0;
+          if ((a > b) == up) {
+            s[i] = b;
+            s[ixj] = a;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < kChunk; i += kChunkThreads)
+    if (base + i < S) data[base + i] = s[i];
+}
+
+constexpr int kMergeTile = 2048;
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = kMergeTile / kMergeThreads;
+
+// number of elements taken from a among the first diag outputs of merge(a, b)
+__device__ __forceinline__ uint64_t merge_split(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb,
+                                                uint64_t diag) {
+  uint64_t lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;
+  while (lo < hi) {
+    uint64_t mid = (lo + hi) >> 1;
+    if (a[mid] <= b[diag - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kMergeThreads) merge_pass_u64(const uint64_t* __restrict__ src,
+                                                                uint64_t* __restrict__ dst, uint64_t S, uint64_t w) {
+  __shared__ uint64_t s[kMergeTile];
+  const uint64_t o0 = (uint64_t)blockIdx.x * kMergeTile;
+  if (o0 >= S) return;
+  const uint64_t o1 = min(S, o0 + kMergeTile);
+  const uint64_t p0 = (o0 / (2 * w)) * (2 * w);
+  const uint64_t a0 = p0, a1 = min(S, p0 + w), b0 = a1, b1 = min(S, p0 + 2 * w);
+  __shared__ uint64_t split[2];
+  if (threadIdx.x < 2) {
+    uint64_t diag = (threadIdx.x ? o1 : o0) - p0;
+    split[threadIdx.x] = merge_split(src + a0, a1 - a0, src + b0, b1 - b0, diag);
+  }
+  __syncthreads();
+  const uint64_t ka0 = split[0], ka1 = split[1];
+  const uint64_t kb0 = (o0 - p0) - ka0, kb1 = (o1 - p0) - ka1;
+  const int na = (int)(ka1 - ka0), nb = (int)(kb1 - kb0);
+  for (int i = threadIdx.x; i < na; i += kMergeThreads) s[i] = src[a0 + ka0 + i];
+  for (int i = threadIdx.x; i < nb; i += kMergeThreads) s[na + i] = src[b0 + kb0 + i];
+  __syncthreads();
+  const int tot = na + nb;
+  int d = threadIdx.x * kMergeItems;
+  if (d >= tot) return;
+  // split of this thread's diagonal inside the tile
+  int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (s[mid] <= s[na + d - 1 - mid]) lo = mid + 1;
+    else hi = mid;
+  }
+  int ia = lo, ib = d - lo;
+  for (int t = 0; t < kMergeItems && d + t < tot; ++t) {
+    bool takeA = ib >= nb || (ia < na && s[ia] <= s[na + ib]);
+    dst[o0 + d + t] = takeA ? s[ia++] : s[na + ib++];
+  }
+}
+
+// ------------------------------------------------------------------ RMI, level by level
+__global__ void init_root(DNode* nodes, uint32_t* pnode, uint64_t S, uint32_t* ctrl) {
+  uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+  if (k == 0) {
+    DNode r = {};
+    r.s = 0;
+    r.e = (uint32_t)S;
+    nodes[0] = r;
+    ctrl[kLevelNodes + 0] = 0;
+    ctrl[kLevelNodes + 1] = 1;
+    ctrl[kLevelNodes + 2] = 0;
+    ctrl[kLevelNodes + 3] = 1;
+  }
+  for (; k < S; k += (uint64_t)gridDim.x * blockDim.x) pnode[k] = 0;
+}
+
+// per-node base and shift, read by every point of the node
+__device__ __forceinline__ void node_frame(const uint64_t* x, uint32_t s, uint32_t e, uint64_t* base, uint32_t* sh) {
+  uint64_t b = x[s];
+  uint64_t span = x[e - 1] - b;
+  uint32_t bits = span ? 64 - __clzll((long long)span) : 0;
+  *base = b;
+  *sh = bits > 32 ? bits - 32 : 0;
+}
+
+// exact sums Su, Suu, Sur of each node of the level (u = local coordinate, r = local rank)
+__global__ void level_sums(const uint64_t* __restrict__ x, uint64_t S, const DNode* __restrict__ nodes,
+                           const uint32_t* __restrict__ pnode, uint64_t* sums, const uint32_t* ctrl) {
+  const uint32_t lv0 = ctrl[kLevelNodes + 0];
+  for (uint64_t k0 = blockIdx.x * (uint64_t)blockDim.x; k0 < S; k0 += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t k = k0 + threadIdx.x;
+    uint32_t v = k < S ? pnode[k] : kSettled;
+    u128 u = 0, uu = 0, ur = 0;
+    if (v != kSettled) {
+      uint32_t s = nodes[v].s, e = nodes[v].e;
+      uint64_t base;
+      uint32_t sh;
+      node_frame(x, s, e, &base, &sh);
+      uint64_t uv = (x[k] - base) >> sh;
+      u = uv;
+      uu = (u128)uv * uv;
+      ur = (u128)uv * (uint64_t)(k - s);
+    }
+    uint32_t v0 = __shfl_sync(0xffffffffu, v, 0);
+    if (__all_sync(0xffffffffu, v == v0) && v0 != kSettled) {
+      for (int d = 16; d; d >>= 1) {
+        u += shfl_down_u128(u, d);
+        uu += shfl_down_u128(uu, d);
+        ur += shfl_down_u128(ur, d);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        uint64_t* sm = sums + (uint64_t)(v0 - lv0) * 6;
+        atomicAdd(reinterpret_cast<unsigned long long*>(sm), (unsigned long long)(uint64_t)u);
+        atomic_add_u128(sm + 2, uu);
+        atomic_add_u128(sm + 4, ur);
+      }
+    } else if (v != kSettled) {
+      uint64_t* sm = sums + (uint64_t)(v - lv0) * 6;
+      atomicAdd(reinterpret_cast<unsigned long long*>(sm), (unsigned long long)(uint64_t)u);
+      atomic_add_u128(sm + 2, uu);
+      atomic_add_u128(sm + 4, ur);
+    }
+  }
+}
+
+// least-squares fit of every node of the level and its split decision
+__global__ void level_fit(const uint64_t* __restrict__ x, uint64_t S, DNode* nodes, const uint64_t* sums,
+                          uint32_t* fc, uint32_t T, uint32_t Dmax, const uint32_t* ctrl) {
+  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
+  for (uint32_t v = lv0 + blockIdx.x * blockDim.x + threadIdx.x; v < lv1; v += gridDim.x * blockDim.x) {
+    DNode nd = nodes[v];
+    uint32_t n = nd.e - nd.s;
+    fc[v - lv0] = 0;
+    if (n == 0) {
+      nd.base = 0;
+      nd.shift = 0;
+      nd.a = 0.0;
+      nd.b = 0.0;
+      nodes[v] = nd;
+      continue;
+    }
+    node_frame(x, nd.s, nd.e, &nd.base, &nd.shift);
+    const uint64_t* sm = sums + (uint64_t)(v - lv0) * 6;
+    u128 Su = sm[0];
+    u128 Suu = ((u128)sm[3] << 64) | sm[2];
+    u128 Sur = ((u128)sm[5] << 64) | sm[4];
+    i128 nn = (i128)n;
+    i128 Sr = nn * (nn - 1) / 2;
+    i128 Duu = nn * (i128)Suu - (i128)Su * (i128)Su;
+    i128 Dur = nn * (i128)Sur - (i128)Su * Sr;
+    double gamma = (n >= 2 && Duu > 0) ? pos_or_zero(__ddiv_rn(i128_to_double(Dur), i128_to_double(Duu))) : 0.0;
+    double delta = __ddiv_rn(__dsub_rn(i128_to_double(Sr), __dmul_rn(gamma, u128_to_double(Su))), __uint2double_rn(n));
+    nd.a = gamma;
+    nd.b = delta;
+    nd.c = 0.0;
+    bool split = n > 2u * T && nd.depth < Dmax && x[nd.s] < x[nd.e - 1];
+    if (split) {
+      uint32_t f = (n + T - 1) / T;
+      nd.fanout = f;
+      nd.c = __ddiv_rn(__uint2double_rn(f), __uint2double_rn(n));
+      if (route(nd, x[nd.s]) == route(nd, x[nd.e - 1])) split = false;
+      nd.fanout = 0;
+      if (split) fc[v - lv0] = f;
+    }
+    nodes[v] = nd;
+  }
+}
+
+constexpr int kScanThreads = 1024;
+
+// Single CTA: child numbering (exclusive scan of fanouts), the node budget,
+// leaf constants, and the next level's node records.
+__global__ void __launch_bounds__(kScanThreads) level_link(DNode* nodes, const uint32_t* fc, uint64_t* sums,
+                                                           uint64_t S, uint64_t node_cap, uint32_t* ctrl) {
+  __shared__ uint32_t wsum[kScanThreads / 32];
+  __shared__ uint32_t total_sh;
+  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
+  const uint32_t cnt = lv1 - lv0;
+  const uint32_t per = (cnt + kScanThreads - 1) / kScanThreads;
+  const uint32_t b = threadIdx.x * per, e = min(cnt, b + per);
+  uint32_t local = 0;
+  for (uint32_t i = b; i < e; ++i) local += fc[i];
+  // block exclusive scan of `local`
+  uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = local;
+  for (int d = 1; d < 32; d <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = wsum[lane];
+    uint32_t wi = w;
+    for (int d = 1; d < 32; d <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= (uint32_t)d) wi += y;
+    }
+    wsum[lane] = wi - w;
+    if (lane == 31) total_sh = wi;
+  }
+  __syncthreads();
+  uint32_t run = wsum[warp] + incl - local;
+  const uint32_t total_nodes = ctrl[kLevelNodes + 3];
+  const uint32_t total = total_sh;
+  const bool overflow = (uint64_t)total_nodes + total > node_cap;
+  const double dS = __ull2double_rn(S);
+  for (uint32_t i = b; i < e; ++i) {
+    uint32_t v = lv0 + i;
+    DNode nd = nodes[v];
+    if (fc[i] && !overflow) {
+      nd.fanout = fc[i];
+      nd.child0 = lv1 + run;
+      nd.c = __ddiv_rn(__uint2double_rn(nd.fanout), __uint2double_rn(nd.e - nd.s));
+      run += fc[i];
+    } else {
+      nd.fanout = 0;
+      nd.child0 = 0;
+      double lo = __ddiv_rn(__uint2double_rn(nd.s), dS), hi = __ddiv_rn(__uint2double_rn(nd.e), dS);
+      if (nd.e == nd.s) {
+        nd.a = 0.0;
+        nd.b = lo;
+      } else {
+        double g = __ddiv_rn(nd.a, dS);
+        double d = __ddiv_rn(__dadd_rn(__uint2double_rn(nd.s), nd.b), dS);
+        nd.a = g;
+        nd.b = d;
+      }
+      nd.c = lo;
+      nd.h = hi;
+    }
+    nodes[v] = nd;
+  }
+  __syncthreads();
+  const uint32_t next = overflow ? 0 : total;
+  const uint32_t depth = nodes[lv0].depth + 1;
+  for (uint32_t w = threadIdx.x; w < next; w += kScanThreads) {
+    DNode c = {};
+    c.depth = depth;
+    nodes[lv1 + w] = c;
+    uint64_t* sm = sums + (uint64_t)w * 6;
+    for (int t = 0; t < 6; ++t) sm[t] = 0;
+  }
+  if (threadIdx.x == 0) {
+    ctrl[kLevelNodes + 2] = next;
+    ctrl[kLevelNodes + 3] = total_nodes + next;
+  }
+}
+
+// route every point of an internal node to its child; children's rank ranges
+__global__ void level_route(const uint64_t* __restrict__ x, uint64_t S, DNode* nodes, uint32_t* pnode,
+                            const uint32_t* ctrl) {
+  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < S; k += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v = pnode[k];
+    if (v == kSettled || v < lv0 || v >= lv1) continue;
+    const DNode nd = nodes[v];
+    if (!nd.fanout) {
+      pnode[k] = kSettled;
+      continue;
+    }
+    uint32_t c = route(nd, x[k]);
+    pnode[k] = nd.child0 + c;
+    int pc = (k == nd.s) ? -1 : (int)route(nd, x[k - 1]);
+    for (int cc = pc + 1; cc <= (int)c; ++cc) {
+      nodes[nd.child0 + cc].s = (uint32_t)k;
+      if (cc >= 1) nodes[nd.child0 + cc - 1].e = (uint32_t)k;
+    }
+    if (k == nd.e - 1) {
+      for (uint32_t cc = c + 1; cc < nd.fanout; ++cc) {
+        nodes[nd.child0 + cc].s = nd.e;
+        nodes[nd.child0 + cc - 1].e = nd.e;
+      }
+      nodes[nd.child0 + nd.fanout - 1].e = nd.e;
+    }
+  }
+}
+
+__global__ void level_advance(uint32_t* ctrl) {
+  uint32_t lv1 = ctrl[kLevelNodes + 1];
+  ctrl[kLevelNodes + 0] = lv1;
+  ctrl[kLevelNodes + 1] = lv1 + ctrl[kLevelNodes + 2];
+}
+
+// fine-bin splitters: t[q] = smallest encoding whose bin is >= q (t[0] = 0);
+// 95^9 when no key reaches bin q
+__global__ void splitter_kernel(const DNode* __restrict__ nodes, uint32_t log2B, uint64_t* t) {
+  const uint32_t B = 1u << log2B;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < B; q += gridDim.x * blockDim.x) {
+    if (q == 0) {
+      t[0] = 0;
+      continue;
+    }
+    uint64_t lo = 0, hi = kEncTop;
+    while (lo < hi) {
+      uint64_t mid = lo + ((hi - lo) >> 1);
+      if (model_bin(nodes, mid, log2B) >= q) hi = mid;
+      else lo = mid + 1;
+    }
+    t[q] = lo;
+  }
+}
+
+__global__ void write_header(ModelHeader h, ModelHeader* dst, const uint32_t* ctrl) {
+  h.num_nodes = ctrl[kLevelNodes + 3];
+  *dst = h;
+}
+
+}  // namespace
+
+uint64_t node_cap_for(uint64_t S, uint32_t T) { return 4 * ((S + T - 1) / T) + 1024; }
+
+size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T) {
+  return 256 + node_cap_for(S, T) * sizeof(DNode) + ((size_t)8 << log2B);
+}
+
+int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&cached, cudaDevAttrMultiProcessorCount, dev);
+    if (cached <= 0) cached = 148;
+  }
+  return cached;
+}
+
+cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out) {
+  const uint64_t S = a.S;
+  const uint64_t cap = node_cap_for(S, a.T);
+  uint8_t* mb = static_cast<uint8_t*>(a.model);
+  ModelHeader h = {};
+  h.magic = kModelMagic;
+  h.kind = 0;
+  h.log2B = a.log2B;
+  h.S = S;
+  h.node_cap = cap;
+  h.nodes_off = 256;
+  h.splitters_off = 256 + cap * sizeof(DNode);
+  h.bytes = model_bytes_for(S, a.log2B, a.T);
+  h.T = a.T;
+  h.Dmax = a.Dmax;
+  DNode* nodes = reinterpret_cast<DNode*>(mb + h.nodes_off);
+  uint64_t* splitters = reinterpret_cast<uint64_t*>(mb + h.splitters_off);
+  const int sms = sm_count();
+  cudaStream_t st = a.stream;
+  uint32_t& L = *a.launches;
+  // 1. sample (Sec. 3.1)
+  const unsigned sgrid = (unsigned)umin64((S + 255) / 256, (uint64_t)sms * 8);
+  sample_kernel<<<sgrid, 256, 0, st>>>(a.records, a.n, S, a.seed, a.samp);
+  ++L;
+  // 2. sort the sample
+  chunk_sort_u64<<<(unsigned)((S + kChunk - 1) / kChunk), kChunkThreads, 0, st>>>(a.samp, S);
+  ++L;
+  uint64_t* src = a.samp;
+  uint64_t* dst = a.samp + S;
+  for (uint64_t w = kChunk; w < S; w *= 2) {
+    merge_pass_u64<<<(unsigned)((S + kMergeTile - 1) / kMergeTile), kMergeThreads, 0, st>>>(src, dst, S, w);
+    ++L;
+    uint64_t* tmp = src;
+    src = dst;
+    dst = tmp;
+  }
+  const uint64_t* x = src;
+  // 3. RMI, breadth first, one level per round
+  cudaMemsetAsync(a.sums, 0, 6 * sizeof(uint64_t), st);
+  const unsigned pgrid = (unsigned)umin64((S + 255) / 256, (uint64_t)sms * 8);
+  init_root<<<pgrid, 256, 0, st>>>(nodes, a.pnode, S, a.ctrl);
+  ++L;
+  uint32_t levels = 0;
+  uint32_t host_ctrl[4] = {0, 1, 0, 1};
+  for (;;) {
+    const uint32_t cnt = host_ctrl[1] - host_ctrl[0];
+    level_sums<<<pgrid, 256, 0, st>>>(x, S, nodes, a.pnode, a.sums, a.ctrl);
+    level_fit<<<(unsigned)umin64((cnt + 255) / 256, (uint64_t)sms * 8), 256, 0, st>>>(
+        x, S, nodes, a.sums, a.fc, a.T, a.Dmax, a.ctrl);
+    level_link<<<1, kScanThreads, 0, st>>>(nodes, a.fc, a.sums, S, cap, a.ctrl);
+    level_route<<<pgrid, 256, 0, st>>>(x, S, nodes, a.pnode, a.ctrl);
+    level_advance<<<1, 1, 0, st>>>(a.ctrl);
+    L += 5;
+    ++levels;
+    cudaError_t err = cudaMemcpyAsync(host_ctrl, a.ctrl + kLevelNodes, sizeof(host_ctrl), cudaMemcpyDeviceToHost, st);
+    if (err != cudaSuccess) return err;
+    err = cudaStreamSynchronize(st);
+    if (err != cudaSuccess) return err;
+    if (host_ctrl[2] == 0 || host_ctrl[0] == host_ctrl[1]) break;
+  }
+  h.levels = levels;
+  // 4. splitters of the fine bins
+  const uint32_t B = 1u << a.log2B;
+  splitter_kernel<<<(B + 127) / 128, 128, 0, st>>>(nodes, a.log2B, splitters);
+  write_header<<<1, 1, 0, st>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
+  L += 2;
+  *nodes_out = host_ctrl[3];
+  return cudaGetLastError();
+}
+
+}  // namespace elsar

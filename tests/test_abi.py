@@ -1,0 +1,70 @@
+"""The C ABI library loads and exports every entry point include/elsar.h declares;
+host-side argument checks answer without touching a GPU."""
+import ctypes
+
+import pytest
+
+import paper_2305_05671_b300 as elsar
+
+
+def test_library_exports_every_declared_symbol():
+    L = elsar.lib()
+    names = elsar.declared_symbols()
+    assert {"elsar_fit_model", "elsar_partition", "elsar_sort_partitions", "elsar_sort"} <= set(names)
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_defaults():
+    p = elsar.default_params()
+    assert p.num_partitions == 1024 and p.balance == elsar.BALANCE_REFINED and p.schedule == elsar.SCHED_PERSISTENT
+
+
+def test_workspace_grows_with_n():
+    p = elsar.Params()
+    small, big = elsar.workspace_size(1000, p), elsar.workspace_size(10**8, p)
+    assert 0 < small < big
+    assert big >= 2 * 16 * 10**8  # two 16-byte pair arrays
+    assert elsar.model_size(10**8, p) > 8 << 17
+
+
+def _status(fn, *args):
+    return fn(*args)
+
+
+FAKE_WS = 1 << 20  # never dereferenced: every case below is rejected before any CUDA call
+
+
+@pytest.mark.parametrize("field,value", [("num_partitions", 1000), ("num_partitions", 1 << 17), ("tile_pairs", 300),
+                                         ("tile_pairs", 1 << 14), ("sample_size", 1 << 24), ("balance", 2),
+                                         ("schedule", 5), ("model_kind", 9), ("fine_bins_log2", 23)])
+def test_bad_params_rejected(field, value):
+    p = elsar.Params(**{field: value})
+    rc = elsar.lib().elsar_sort(FAKE_WS, FAKE_WS * 2, 1000, ctypes.byref(p.c()), FAKE_WS, 1 << 40, None, None)
+    assert rc == 1
+    assert elsar.lib().elsar_last_error()
+
+
+def test_sizes_and_buffers_rejected_on_host():
+    L = elsar.lib()
+    p = elsar.Params().c()
+    assert L.elsar_sort(FAKE_WS, FAKE_WS * 2, 1 << 32, ctypes.byref(p), FAKE_WS, 1 << 60, None, None) == 5
+    assert L.elsar_sort(FAKE_WS, FAKE_WS * 2, 1000, ctypes.byref(p), FAKE_WS, 10, None, None) == 2
+    assert L.elsar_sort(FAKE_WS, FAKE_WS * 2, 1000, ctypes.byref(p), FAKE_WS + 8, 1 << 40, None, None) == 1
+    assert L.elsar_sort(FAKE_WS + 1, FAKE_WS * 2, 1000, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 1
+    # overlapping input and output
+    assert L.elsar_sort(FAKE_WS, FAKE_WS + 400, 1000, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 1
+    assert L.elsar_fit_model(FAKE_WS, 0, ctypes.byref(p), FAKE_WS, 1 << 30, FAKE_WS, 1 << 40, None) == 1
+    # n == 0 is a no-op
+    assert L.elsar_sort(None, None, 0, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 0
+
+
+def test_status_strings():
+    L = elsar.lib()
+    for s in range(7):
+        assert L.elsar_status_str(s)
+
+
+def test_binding_raises():
+    with pytest.raises(elsar.ElsarError):
+        elsar._check(2)
