@@ -163,6 +163,33 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
 elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_in,
                              void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
 
+/* Bytes of the scratch area built into the library for elsar_sort_noalloc. */
+#define ELSAR_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * elsar_sort for callers that cannot allocate device memory (no cudaMalloc
+ * allowed or possible: plugins and callbacks whose runtime forbids it, memory
+ * fully owned by another allocator, code that must not risk cudaFree's
+ * device-wide synchronisation).  The paper has no counterpart; this is an
+ * interface addition.  The caller passes the input and output records only;
+ * scratch comes from a fixed array of ELSAR_NOALLOC_SCRATCH_BYTES (16 MiB)
+ * compiled into the library, which every GPU that loads the library keeps
+ * until the process exits.  The limit: elsar_workspace_size(n, p) must fit in
+ * it -- about 500,000 records with the default parameters -- else the call
+ * returns ELSAR_EUNSUPPORTED and allocates nothing.  The call allocates no
+ * device memory itself (no cudaMalloc/cudaFree, no allocating library call).
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on one device share the one scratch
+ * array and it keeps the previous call's contents (each call clears what
+ * must start at zero): calls that can overlap on the GPU -- on different
+ * streams, or from different threads -- race on it and must be serialised by
+ * the caller.  Synchronises `stream` like elsar_sort.
+ */
+elsar_status elsar_sort_noalloc(const void* d_in, void* d_out, uint64_t n, const elsar_params* p,
+                                elsar_stream_t stream);
+
 /* Static description of a status code. */
 const char* elsar_status_str(elsar_status s);
 

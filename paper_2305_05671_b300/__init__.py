@@ -80,6 +80,7 @@ def lib():
             "elsar_sort_partitions": (ctypes.c_int, [P, U64, PP, P, P, P, P, SZ, P]),
             "elsar_sort": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_Stats)]),
             "elsar_sort_host": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
+            "elsar_sort_noalloc": (ctypes.c_int, [P, P, U64, PP, P]),
             "elsar_status_str": (ctypes.c_char_p, [ctypes.c_int]),
             "elsar_last_error": (ctypes.c_char_p, []),
         }
@@ -171,6 +172,11 @@ def sort(d_in, d_out, n: int, p: Params | None = None, ws=None, stream=None, sta
     return dict(pass_ms=list(st.pass_ms)[:5], launches=st.launches, num_items=st.num_items,
                 oversize_items=st.oversize_items, model_nodes=st.model_nodes, max_partition=st.max_partition,
                 max_bin=st.max_bin)
+
+
+def sort_noalloc(d_in, d_out, n: int, p: Params | None = None, stream=None):
+    """Sort without any workspace: the library's built-in scratch array (small n only)."""
+    _check(lib().elsar_sort_noalloc(_ptr(d_in), _ptr(d_out), n, ctypes.byref((p or Params()).c()), _stream(stream)))
 
 
 def sort_host(h_in, h_out, n: int, p: Params, d_in, d_out, ws, stream=None):

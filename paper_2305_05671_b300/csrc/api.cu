@@ -10,6 +10,7 @@
 
 namespace elsar {
 size_t sort_smem_bytes(uint32_t cap);
+void set_last_error(const char* msg);
 }
 
 using namespace elsar;
@@ -223,6 +224,8 @@ elsar_status do_sort_partitions(const void* d_records, uint64_t n, const Resolve
 }
 
 }  // namespace
+
+void elsar::set_last_error(const char* msg) { g_err = msg; }
 
 extern "C" {
 
