@@ -72,7 +72,7 @@ elsar_status resolve(uint64_t n, const elsar_params* p, Resolved* r) {
   if (r->balance > 1) return fail(ELSAR_EINVAL, "unknown balance rule");
   r->schedule = q.schedule;
   if (r->schedule > 1) return fail(ELSAR_EINVAL, "unknown schedule");
-  r->cap = q.tile_pairs ? q.tile_pairs : 4096;
+  r->cap = q.tile_pairs ? q.tile_pairs : 2048;
   if (!pow2(r->cap) || r->cap < 256 || r->cap > 8192) return fail(ELSAR_EINVAL, "tile_pairs must be a power of two in [256, 8192]");
   if (q.sample_size) {
     r->S = q.sample_size;
@@ -118,7 +118,7 @@ Layout layout(uint64_t n, const Resolved& r) {
   L.samp = take(2 * r.S * 8);
   L.pnode = take(r.S * 4);
   L.sums = take(cap * 48);
-  L.fc = take(cap * 4);
+  L.fc = take(cap * 8);  // split fanouts + child offsets of one level
   L.total = o;
   return L;
 }
@@ -138,6 +138,7 @@ elsar_status common_checks(uint64_t n, const void* d_ws, size_t ws_bytes, const 
 }
 
 const uint64_t* splitters_in(const void* d_model, const Resolved& r) {
+  if (!d_model) return nullptr;
   return reinterpret_cast<const uint64_t*>(static_cast<const uint8_t*>(d_model) + 256 +
                                            node_cap_for(r.S, r.T) * sizeof(DNode));
 }
@@ -173,6 +174,7 @@ PartArgs part_args(const void* d_model, const void* d_records, uint64_t n, const
   a.records = static_cast<const uint8_t*>(d_records);
   a.n = n;
   a.splitters = splitters_in(d_model, r);
+  a.lut = d_model ? reinterpret_cast<const uint32_t*>(a.splitters + (1ull << r.log2B)) : nullptr;
   a.log2B = r.log2B;
   a.P = r.P;
   a.balance = r.balance;
@@ -220,6 +222,17 @@ elsar_status do_sort_partitions(const void* d_records, uint64_t n, const Resolve
   s.launches = launches;
   e = sort_items(s);
   if (e != cudaSuccess) return cuda_fail(e, "sort");
+  return ELSAR_OK;
+}
+
+// Device-side failures (a bounded wait that gave up) are latched in the
+// workspace status word; read it back (synchronises the stream).
+elsar_status device_status(void* d_ws, const Layout& L, cudaStream_t st) {
+  uint32_t w = 0;
+  cudaError_t e = cudaMemcpyAsync(&w, at<uint32_t>(d_ws, L.ctrl) + kStatusWord, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "status");
+  if (w) return fail(ELSAR_ETIMEOUT, "a device-side wait timed out (status word %u)", w);
   return ELSAR_OK;
 }
 
@@ -355,8 +368,9 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
   if (s == ELSAR_OK)
     s = do_sort_partitions(d_in, n, r, at<void>(d_ws, L.pairsB), at<uint32_t>(d_ws, L.bin_off), d_out, d_ws, L, st,
                            &launches, ev[5]);
+  if (s == ELSAR_OK && stats) cudaEventRecord(ev[6], st);
+  if (s == ELSAR_OK) s = device_status(d_ws, L, st);
   if (s == ELSAR_OK && stats) {
-    cudaEventRecord(ev[6], st);
     cudaError_t e = cudaEventSynchronize(ev[6]);
     if (e != cudaSuccess) {
       s = cuda_fail(e, "sort");

@@ -10,7 +10,7 @@ constexpr int kRecord = 100;
 constexpr uint64_t kEncTop = 630249409724609375ull;  // 95^9: one past the largest 9-character encoding
 constexpr uint32_t kModelMagic = 0x52534C45u;        // "ELSR"
 constexpr uint32_t kSettled = 0xFFFFFFFFu;           // sample point whose RMI node is already a leaf
-constexpr int kCoarse = 4096;                        // splitter entries kept in shared memory for classification
+constexpr int kCoarse = 4096;                        // splitters kept in shared memory for classification
 
 // 16-byte sort pair (the paper's pointer-only record, Sec. 3.3): ordering by
 // (hi, lo) is memcmp order of the 10-byte key, then input order.
@@ -86,18 +86,66 @@ __device__ __forceinline__ Pair load_pair(const uint8_t* rec, uint32_t idx) {
   return p;
 }
 
-// Fine bin of a key encoding from the splitters t[0..B) (t[0] = 0):
-// q = largest j with t[j] <= x.  ct = every G-th splitter in shared memory.
-__device__ __forceinline__ uint32_t fine_bin(const uint64_t* __restrict__ t, const uint64_t* ct, uint32_t ncoarse,
-                                             uint32_t G, uint64_t x) {
-  uint32_t pos = 0;
-  for (uint32_t step = ncoarse >> 1; step; step >>= 1)
-    if (ct[pos + step] <= x) pos += step;
-  pos *= G;
-  for (uint32_t step = G >> 1; step; step >>= 1)
-    if (__ldg(t + pos + step) <= x) pos += step;
-  return pos;
+// ---------------------------------------------------------------- radix index of the splitters
+// lut[c] = largest q with t[q] <= c << kFineLutShift, for c in [0, kFineLutCells)
+constexpr int kFineLutShift = 42;
+constexpr uint32_t kFineLutCells = (uint32_t)((kEncTop - 1) >> kFineLutShift) + 2;
+
+// q = largest j with t[j] <= x, via the radix index then a binary search
+__device__ __forceinline__ uint32_t splitter_search(const uint64_t* __restrict__ t, const uint32_t* __restrict__ lut,
+                                                    uint64_t x) {
+  const uint32_t c = (uint32_t)(x >> kFineLutShift);
+  uint32_t lo = __ldg(lut + c), hi = __ldg(lut + c + 1);
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (__ldg(t + mid) <= x) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
 }
+
+// ---------------------------------------------------------------- bulk copies (TMA) and mbarriers
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase: false after `limit` clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > limit) return false;
+  return true;
+}
+
+constexpr long long kWaitLimitCycles = 2000000000ll;  // about one second at B300 clocks
 
 // ---------------------------------------------------------------- launchers
 struct FitArgs {
@@ -110,7 +158,7 @@ struct FitArgs {
   uint64_t* samp;   // 2*S
   uint32_t* pnode;  // S
   uint64_t* sums;   // node_cap * 6
-  uint32_t* fc;     // node_cap
+  uint32_t* fc;     // 2 * node_cap: split fanouts, child offsets
   uint32_t* ctrl;   // 64 words
   cudaStream_t stream;
   uint32_t* launches;
@@ -124,6 +172,7 @@ struct PartArgs {
   const uint8_t* records;
   uint64_t n;
   const uint64_t* splitters;  // B fine-bin splitters of the fitted model
+  const uint32_t* lut;        // radix index of the splitters
   uint32_t log2B, P, balance, tile_pairs;
   void* pairs_in_order;  // n pairs (scratch)
   void* pairs;           // n pairs, bin-ordered (output)
@@ -170,9 +219,8 @@ enum Ctrl : int {
   kQueueHead = 2,
   kMaxBin = 3,
   kStatus = 4,
-  kLevelNodes = 8,  // fit: [8] level begin, [9] level end, [10] next level count, [11] total nodes
-  kOversizeHead = 12,
-  kItemsCapped = 13,
+  kLevelNodes = 8,  // fit: [8] level begin, [9] level end, [10] next level count, [11] total nodes, [12] overflow
+  kStatusWord = 16,
 };
 
 }  // namespace elsar

@@ -288,61 +288,81 @@ __global__ void level_fit(const uint64_t* __restrict__ x, uint64_t S, DNode* nod
 
 constexpr int kScanThreads = 1024;
 
-// Single CTA: child numbering (exclusive scan of fanouts), the node budget,
-// leaf constants, and the next level's node records.
-__global__ void __launch_bounds__(kScanThreads) level_link(DNode* nodes, const uint32_t* fc, uint64_t* sums,
-                                                           uint64_t S, uint64_t node_cap, uint32_t* ctrl) {
+// Single CTA: child numbering = exclusive scan of the split fanouts of the
+// level (coalesced tiles of kScanThreads with a running carry) and the node
+// budget check.  ctrl[kLevelNodes+2] = next level size (0 on overflow),
+// ctrl[kLevelNodes+4] = 1 when the budget forbids splitting this level.
+__global__ void __launch_bounds__(kScanThreads) level_scan(const uint32_t* __restrict__ fc, uint32_t* __restrict__ childoff,
+                                                           uint64_t node_cap, uint32_t* ctrl) {
   __shared__ uint32_t wsum[kScanThreads / 32];
-  __shared__ uint32_t total_sh;
+  __shared__ uint32_t carry_sh;
   const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
   const uint32_t cnt = lv1 - lv0;
-  const uint32_t per = (cnt + kScanThreads - 1) / kScanThreads;
-  const uint32_t b = threadIdx.x * per, e = min(cnt, b + per);
-  uint32_t local = 0;
-  for (uint32_t i = b; i < e; ++i) local += fc[i];
-  // block exclusive scan of `local`
-  uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = local;
-  for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= (uint32_t)d) incl += y;
-  }
-  if (lane == 31) wsum[warp] = incl;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_sh = 0;
   __syncthreads();
-  if (warp == 0) {
-    uint32_t w = wsum[lane];
-    uint32_t wi = w;
+  for (uint32_t base = 0; base < cnt; base += kScanThreads) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t v = i < cnt ? fc[i] : 0;
+    uint32_t incl = v;
     for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
-      if (lane >= (uint32_t)d) wi += y;
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= (uint32_t)d) incl += y;
     }
-    wsum[lane] = wi - w;
-    if (lane == 31) total_sh = wi;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const uint32_t w = wsum[lane];
+      uint32_t wi = w;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+        if (lane >= (uint32_t)d) wi += y;
+      }
+      wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    const uint32_t carry = carry_sh;
+    if (i < cnt) childoff[i] = carry + wsum[warp] + incl - v;
+    __syncthreads();
+    if (threadIdx.x == kScanThreads - 1) carry_sh = carry + wsum[warp] + incl;
+    __syncthreads();
   }
-  __syncthreads();
-  uint32_t run = wsum[warp] + incl - local;
-  const uint32_t total_nodes = ctrl[kLevelNodes + 3];
-  const uint32_t total = total_sh;
-  const bool overflow = (uint64_t)total_nodes + total > node_cap;
+  if (threadIdx.x == 0) {
+    const uint32_t total = carry_sh;
+    const uint32_t total_nodes = ctrl[kLevelNodes + 3];
+    const bool overflow = (uint64_t)total_nodes + total > node_cap;
+    const uint32_t next = overflow ? 0 : total;
+    ctrl[kLevelNodes + 2] = next;
+    ctrl[kLevelNodes + 3] = total_nodes + next;
+    ctrl[kLevelNodes + 4] = overflow ? 1u : 0u;
+  }
+}
+
+// Every node of the level: internal nodes get their children, the rest
+// become leaves with their output constants (Sec. 3.1 reading: F clamped to
+// the leaf's sample-rank range).
+__global__ void level_finalize(DNode* nodes, const uint32_t* __restrict__ fc, const uint32_t* __restrict__ childoff,
+                               uint64_t S, const uint32_t* ctrl) {
+  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
+  const bool overflow = ctrl[kLevelNodes + 4] != 0;
   const double dS = __ull2double_rn(S);
-  for (uint32_t i = b; i < e; ++i) {
-    uint32_t v = lv0 + i;
+  for (uint32_t v = lv0 + blockIdx.x * blockDim.x + threadIdx.x; v < lv1; v += gridDim.x * blockDim.x) {
+    const uint32_t i = v - lv0;
     DNode nd = nodes[v];
     if (fc[i] && !overflow) {
       nd.fanout = fc[i];
-      nd.child0 = lv1 + run;
+      nd.child0 = lv1 + childoff[i];
       nd.c = __ddiv_rn(__uint2double_rn(nd.fanout), __uint2double_rn(nd.e - nd.s));
-      run += fc[i];
     } else {
       nd.fanout = 0;
       nd.child0 = 0;
-      double lo = __ddiv_rn(__uint2double_rn(nd.s), dS), hi = __ddiv_rn(__uint2double_rn(nd.e), dS);
+      const double lo = __ddiv_rn(__uint2double_rn(nd.s), dS), hi = __ddiv_rn(__uint2double_rn(nd.e), dS);
       if (nd.e == nd.s) {
         nd.a = 0.0;
         nd.b = lo;
       } else {
-        double g = __ddiv_rn(nd.a, dS);
-        double d = __ddiv_rn(__dadd_rn(__uint2double_rn(nd.s), nd.b), dS);
+        const double g = __ddiv_rn(nd.a, dS);
+        const double d = __ddiv_rn(__dadd_rn(__uint2double_rn(nd.s), nd.b), dS);
         nd.a = g;
         nd.b = d;
       }
@@ -351,19 +371,19 @@ __global__ void __launch_bounds__(kScanThreads) level_link(DNode* nodes, const u
     }
     nodes[v] = nd;
   }
-  __syncthreads();
-  const uint32_t next = overflow ? 0 : total;
+}
+
+// Records of the next level (depth + 1, ranges set by level_route) and their sums zeroed.
+__global__ void level_init_next(DNode* nodes, uint64_t* sums, const uint32_t* ctrl) {
+  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1], next = ctrl[kLevelNodes + 2];
+  if (lv0 >= lv1) return;
   const uint32_t depth = nodes[lv0].depth + 1;
-  for (uint32_t w = threadIdx.x; w < next; w += kScanThreads) {
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < next; w += gridDim.x * blockDim.x) {
     DNode c = {};
     c.depth = depth;
     nodes[lv1 + w] = c;
     uint64_t* sm = sums + (uint64_t)w * 6;
     for (int t = 0; t < 6; ++t) sm[t] = 0;
-  }
-  if (threadIdx.x == 0) {
-    ctrl[kLevelNodes + 2] = next;
-    ctrl[kLevelNodes + 3] = total_nodes + next;
   }
 }
 
@@ -421,6 +441,17 @@ __global__ void splitter_kernel(const DNode* __restrict__ nodes, uint32_t log2B,
   }
 }
 
+// radix index of the splitters: cells c with t[q] <= c << 42 < t[q+1] hold q
+__global__ void fine_lut_kernel(const uint64_t* __restrict__ t, uint32_t log2B, uint32_t* __restrict__ lut) {
+  const uint32_t B = 1u << log2B;
+  const uint64_t cell = 1ull << kFineLutShift;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < B; q += gridDim.x * blockDim.x) {
+    const uint64_t c0 = (t[q] + cell - 1) >> kFineLutShift;
+    const uint64_t c1 = q + 1 < B ? (t[q + 1] + cell - 1) >> kFineLutShift : (uint64_t)kFineLutCells;
+    for (uint64_t c = c0; c < c1 && c < kFineLutCells; ++c) lut[c] = q;
+  }
+}
+
 __global__ void write_header(ModelHeader h, ModelHeader* dst, const uint32_t* ctrl) {
   h.num_nodes = ctrl[kLevelNodes + 3];
   *dst = h;
@@ -431,7 +462,7 @@ __global__ void write_header(ModelHeader h, ModelHeader* dst, const uint32_t* ct
 uint64_t node_cap_for(uint64_t S, uint32_t T) { return 4 * ((S + T - 1) / T) + 1024; }
 
 size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T) {
-  return 256 + node_cap_for(S, T) * sizeof(DNode) + ((size_t)8 << log2B);
+  return 256 + node_cap_for(S, T) * sizeof(DNode) + ((size_t)8 << log2B) + (size_t)kFineLutCells * 4;
 }
 
 int sm_count() {
@@ -494,10 +525,13 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out) {
     level_sums<<<pgrid, 256, 0, st>>>(x, S, nodes, a.pnode, a.sums, a.ctrl);
     level_fit<<<(unsigned)umin64((cnt + 255) / 256, (uint64_t)sms * 8), 256, 0, st>>>(
         x, S, nodes, a.sums, a.fc, a.T, a.Dmax, a.ctrl);
-    level_link<<<1, kScanThreads, 0, st>>>(nodes, a.fc, a.sums, S, cap, a.ctrl);
+    const unsigned ngrid = (unsigned)umin64((cnt + 255) / 256, (uint64_t)sms * 8);
+    level_scan<<<1, kScanThreads, 0, st>>>(a.fc, a.fc + cap, cap, a.ctrl);
+    level_finalize<<<ngrid, 256, 0, st>>>(nodes, a.fc, a.fc + cap, S, a.ctrl);
+    level_init_next<<<(unsigned)umin64((2 * cnt + 255) / 256 + 1, (uint64_t)sms * 8), 256, 0, st>>>(nodes, a.sums, a.ctrl);
     level_route<<<pgrid, 256, 0, st>>>(x, S, nodes, a.pnode, a.ctrl);
     level_advance<<<1, 1, 0, st>>>(a.ctrl);
-    L += 5;
+    L += 7;
     ++levels;
     cudaError_t err = cudaMemcpyAsync(host_ctrl, a.ctrl + kLevelNodes, sizeof(host_ctrl), cudaMemcpyDeviceToHost, st);
     if (err != cudaSuccess) return err;
@@ -509,8 +543,10 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out) {
   // 4. splitters of the fine bins
   const uint32_t B = 1u << a.log2B;
   splitter_kernel<<<(B + 127) / 128, 128, 0, st>>>(nodes, a.log2B, splitters);
+  fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, a.log2B,
+                                                   reinterpret_cast<uint32_t*>(splitters + B));
   write_header<<<1, 1, 0, st>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
-  L += 2;
+  L += 3;
   *nodes_out = host_ctrl[3];
   return cudaGetLastError();
 }

@@ -10,43 +10,116 @@ inline uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 inline uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 
 constexpr int kThreads = 256;
-constexpr int kUnroll = 4;
+constexpr int kUnroll = 8;
+constexpr int kTileRecs = kThreads;  // records staged per bulk copy (25,600 bytes)
+constexpr int kStages = 2;
+constexpr uint32_t kTileBytes = kTileRecs * kRecord;
 
-// splitter table -> shared coarse table (every G-th splitter)
-__device__ __forceinline__ void load_coarse(const uint64_t* __restrict__ t, uint32_t log2B, uint64_t* ct,
-                                            uint32_t* ncoarse, uint32_t* G) {
-  const uint32_t B = 1u << log2B;
-  const uint32_t nc = B < (uint32_t)kCoarse ? B : (uint32_t)kCoarse;
-  const uint32_t g = B / nc;
-  for (uint32_t i = threadIdx.x; i < nc; i += blockDim.x) ct[i] = t[(uint64_t)i * g];
-  *ncoarse = nc;
-  *G = g;
-  __syncthreads();
+__device__ __forceinline__ void classify_one(const Pair& key, uint64_t i, const uint64_t* __restrict__ t,
+                                             const uint32_t* __restrict__ lut, Pair* __restrict__ pairs,
+                                             uint32_t* __restrict__ hist) {
+  Pair p = key;
+  const uint32_t q = splitter_search(t, lut, enc9_pair(p));
+  p.lo |= q;
+  pairs[i] = p;
+  atomicAdd(hist + q, 1u);
 }
 
-// Pass A: every record -> (pair in input order, fine bin histogram).
+__device__ __forceinline__ Pair pair_from_words(uint32_t a, uint32_t b, uint32_t c) {
+  Pair p;
+  p.hi = ((uint64_t)__byte_perm(a, 0, 0x0123) << 32) | __byte_perm(b, 0, 0x0123);
+  p.lo = (uint64_t)__byte_perm(c, 0, 0x4401) << 32;
+  return p;
+}
+
+// Pass A, TMA form: tiles of 256 records (25,600 bytes, 16-byte aligned when
+// the record buffer is) are bulk-copied into shared memory, double buffered
+// on mbarriers; each thread packs one key from shared memory, classifies it
+// and counts it.  The input-order pair carries {hi, (key bytes 8-9) << 32 | q}.
+// Every wait is bounded: on timeout the CTA raises the status word, waits
+// (bounded) for its own copies in flight and leaves.
+__global__ void __launch_bounds__(kThreads) classify_tma_kernel(const uint8_t* __restrict__ rec, uint64_t n,
+                                                                const uint64_t* __restrict__ t,
+                                                                const uint32_t* __restrict__ lut,
+                                                                Pair* __restrict__ pairs, uint32_t* __restrict__ hist,
+                                                                uint32_t* ctrl) {
+  extern __shared__ __align__(128) uint8_t buf[];  // kStages x kTileBytes
+  __shared__ uint64_t bar[kStages];
+  const uint64_t ntiles = n / kTileRecs;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t issued[kStages] = {};  // copies issued per stage (thread 0)
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      const uint64_t k = blockIdx.x + (uint64_t)s * gridDim.x;
+      if (k < ntiles) {
+        mbar_expect_tx(&bar[s], kTileBytes);
+        bulk_g2s(buf + s * kTileBytes, rec + k * kTileBytes, kTileBytes, &bar[s]);
+        issued[s] = 1;
+      }
+    }
+  }
+  bool failed = false;
+  uint32_t j = 0;
+  for (uint64_t k = blockIdx.x; k < ntiles; k += gridDim.x, ++j) {
+    const int s = j % kStages;
+    const uint32_t parity = (j / kStages) & 1;
+    const bool ok = mbar_wait(&bar[s], parity, kWaitLimitCycles);
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const uint32_t* w = reinterpret_cast<const uint32_t*>(buf + s * kTileBytes + threadIdx.x * kRecord);
+    const uint64_t i = k * kTileRecs + threadIdx.x;
+    classify_one(pair_from_words(w[0], w[1], w[2]), i, t, lut, pairs, hist);
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0) {
+      const uint64_t k2 = k + (uint64_t)kStages * gridDim.x;
+      if (k2 < ntiles) {
+        fence_proxy_async();
+        mbar_expect_tx(&bar[s], kTileBytes);
+        bulk_g2s(buf + s * kTileBytes, rec + k2 * kTileBytes, kTileBytes, &bar[s]);
+        ++issued[s];
+      }
+    }
+  }
+  if (failed) {
+    if (threadIdx.x == 0) {
+      atomicOr(ctrl + kStatusWord, 1u);
+      // copies still in flight target this CTA's shared memory: wait for them, bounded
+      for (int s = 0; s < kStages; ++s) {
+        // stage s completed (j_s) phases so far; its last issued copy ends phase issued[s]-1
+        if (issued[s]) mbar_wait(&bar[s], (issued[s] - 1) & 1, kWaitLimitCycles);
+      }
+    }
+    return;
+  }
+  // ragged tail (n mod 256 records): plain loads
+  for (uint64_t i = ntiles * kTileRecs + blockIdx.x * (uint64_t)kThreads + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * kThreads)
+    classify_one(load_pair(rec + i * kRecord, 0), i, t, lut, pairs, hist);
+}
+
+// Pass A, plain form (record buffers that are not 16-byte aligned).
 __global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __restrict__ rec, uint64_t n,
-                                                            const uint64_t* __restrict__ t, uint32_t log2B,
+                                                            const uint64_t* __restrict__ t,
+                                                            const uint32_t* __restrict__ lut,
                                                             Pair* __restrict__ pairs, uint32_t* __restrict__ hist) {
-  __shared__ uint64_t ct[kCoarse];
-  uint32_t nc, G;
-  load_coarse(t, log2B, ct, &nc, &G);
   const uint64_t stride = (uint64_t)gridDim.x * kThreads * kUnroll;
   for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads * kUnroll + threadIdx.x; i0 < n; i0 += stride) {
     Pair p[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      uint64_t i = i0 + (uint64_t)u * kThreads;
-      if (i < n) p[u] = load_pair(rec + i * kRecord, (uint32_t)i);
+      const uint64_t i = i0 + (uint64_t)u * kThreads;
+      if (i < n) p[u] = load_pair(rec + i * kRecord, 0);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      uint64_t i = i0 + (uint64_t)u * kThreads;
-      if (i < n) {
-        uint32_t q = fine_bin(t, ct, nc, G, enc9_pair(p[u]));
-        pairs[i] = p[u];
-        atomicAdd(hist + q, 1u);
-      }
+      const uint64_t i = i0 + (uint64_t)u * kThreads;
+      if (i < n) classify_one(p[u], i, t, lut, pairs, hist);
     }
   }
 }
@@ -194,28 +267,32 @@ __global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __r
   }
 }
 
-// Pass B: pairs (input order) -> bin order; slot from an atomic cursor per bin.
+// Pass B: pairs (input order) -> bin order; slot from an atomic cursor per
+// bin; the fine bin rides in the pair, the record index replaces it.
 __global__ void __launch_bounds__(kThreads) scatter_kernel(const Pair* __restrict__ in, uint64_t n,
-                                                           const uint64_t* __restrict__ t, uint32_t log2B,
                                                            uint32_t* __restrict__ cursor, Pair* __restrict__ out) {
-  __shared__ uint64_t ct[kCoarse];
-  uint32_t nc, G;
-  load_coarse(t, log2B, ct, &nc, &G);
   const uint64_t stride = (uint64_t)gridDim.x * kThreads * kUnroll;
   for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads * kUnroll + threadIdx.x; i0 < n; i0 += stride) {
     Pair p[kUnroll];
+    uint32_t slot[kUnroll];
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      uint64_t i = i0 + (uint64_t)u * kThreads;
+      const uint64_t i = i0 + (uint64_t)u * kThreads;
       if (i < n) p[u] = in[i];
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
-      uint64_t i = i0 + (uint64_t)u * kThreads;
+      const uint64_t i = i0 + (uint64_t)u * kThreads;
+      if (i < n) slot[u] = atomicAdd(cursor + (uint32_t)p[u].lo, 1u);
+    }
+#pragma unroll
+    for (int u = 0; u < kUnroll; ++u) {
+      const uint64_t i = i0 + (uint64_t)u * kThreads;
       if (i < n) {
-        uint32_t q = fine_bin(t, ct, nc, G, enc9_pair(p[u]));
-        uint32_t slot = atomicAdd(cursor + q, 1u);
-        out[slot] = p[u];
+        Pair o;
+        o.hi = p[u].hi;
+        o.lo = (p[u].lo & 0xFFFFFFFF00000000ull) | (uint32_t)i;
+        out[slot[u]] = o;
       }
     }
   }
@@ -228,18 +305,34 @@ cudaError_t partition_records(const PartArgs& a) {
   cudaStream_t st = a.stream;
   const int sms = sm_count();
   cudaMemsetAsync(a.cursor, 0, (size_t)B * 4, st);  // the histogram lives in `cursor` until the scan
-  cudaMemsetAsync(a.ctrl, 0, 64, st);
+  cudaMemsetAsync(a.ctrl, 0, 32 * sizeof(uint32_t), st);
   const uint64_t per_block = (uint64_t)kThreads * kUnroll;
-  const unsigned grid = (unsigned)umax64(1, umin64((a.n + per_block - 1) / per_block, (uint64_t)sms * 8));
-  classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.log2B,
-                                             static_cast<Pair*>(a.pairs_in_order), a.cursor);
+  const uint64_t blocks = (a.n + per_block - 1) / per_block;
+  int occ_s = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, scatter_kernel, kThreads, 0);
+  const unsigned grid_s = (unsigned)umax64(1, umin64(blocks, (uint64_t)sms * (occ_s > 0 ? occ_s : 1)));
+  Pair* pin = static_cast<Pair*>(a.pairs_in_order);
+  if ((reinterpret_cast<uintptr_t>(a.records) & 15) == 0) {
+    const size_t smem = (size_t)kStages * kTileBytes;
+    cudaFuncSetAttribute(classify_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_tma_kernel, kThreads, smem);
+    const uint64_t tiles = a.n / kTileRecs;
+    const unsigned grid = (unsigned)umax64(1, umin64(tiles, (uint64_t)sms * (occ > 0 ? occ : 1)));
+    classify_tma_kernel<<<grid, kThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl);
+  } else {
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_kernel, kThreads, 0);
+    const unsigned grid = (unsigned)umax64(1, umin64(blocks, (uint64_t)sms * (occ > 0 ? occ : 1)));
+    classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor);
+  }
   if (a.ev[0]) cudaEventRecord(a.ev[0], st);
   scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.log2B, a.bin_off, a.cursor, a.ctrl);
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       nullptr);
   if (a.ev[1]) cudaEventRecord(a.ev[1], st);
-  scatter_kernel<<<grid, kThreads, 0, st>>>(static_cast<const Pair*>(a.pairs_in_order), a.n, a.splitters, a.log2B,
-                                            a.cursor, static_cast<Pair*>(a.pairs));
+  scatter_kernel<<<grid_s, kThreads, 0, st>>>(static_cast<const Pair*>(a.pairs_in_order), a.n, a.cursor,
+                                            static_cast<Pair*>(a.pairs));
   if (a.ev[2]) cudaEventRecord(a.ev[2], st);
   *a.launches += 4;
   return cudaGetLastError();

@@ -1,9 +1,10 @@
 // Sorting every partition and concatenating (Sec. 3.4, Sec. 3.5, and the
 // touch-up of Sec. 4) on the GPU.  A work item is a run of consecutive fine
 // bins (model sub-buckets) of one partition holding at most `cap` pairs.  One
-// CTA sorts an item in shared memory -- a counting sort on the leading bits
-// of the key below the item's common prefix (the model-style placement),
-// then a per-run touch-up by insertion sort (bitonic for long runs) -- and
+// CTA sorts an item in shared memory -- a counting sort on the leading bits of
+// the keys' base-95 encoding below the item's common prefix (a placement by
+// value, like the model's), long runs refined the same way by warps on their
+// own key range, short runs finished by insertion sort (the touch-up) -- and
 // gathers the 100-byte records of the item, in order, straight into their
 // final place in the output, so the partitions come out concatenated with no
 // merge.  Items above `cap` pairs (heavy duplicate keys) take a multi-pass
@@ -17,20 +18,31 @@
 namespace elsar {
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kLongMax = 64;
-constexpr uint32_t kSent = 0xFFFFFFFFu;
+constexpr uint32_t kShortRun = 16;  // runs up to this length get the insertion-sort touch-up
 
 struct Misc {
   uint64_t red[2][kWarps];
   uint64_t kmin, kmax;
-  uint32_t use_lo;
-  uint32_t nlong;
-  uint32_t long_start[kLongMax], long_len[kLongMax];
+  uint32_t nlong, next_long;
+  uint32_t stk_top[kWarps];
   uint32_t item;
   uint64_t split[2];
   uint32_t wsum[33];
+};
+
+// Shared-memory tile of one work item.  Runs are packed as (start << 16) | length.
+struct Tile {
+  Pair* A;         // cap pairs
+  uint64_t* E;     // cap base-95 encodings of the first 9 key bytes
+  uint32_t* cnt;   // cap digit counters
+  uint16_t* perm;  // cap: sorted order being built
+  uint16_t* perm2; // cap: scatter target
+  uint32_t* longs; // cap/16 + 1 long runs of the first digit pass
+  uint32_t* stk;   // kWarps x (cap/16 + 1) refinement stacks
+  uint32_t stk_cap;
+  Misc* ms;
 };
 
 struct KArgs {
@@ -47,7 +59,12 @@ struct KArgs {
   int persistent;
 };
 
-__device__ __forceinline__ uint64_t key_of(const Pair& p, bool use_lo) { return use_lo ? p.lo : p.hi; }
+// key used by a digit pass: 0 = base-95 encoding (dense for printable keys),
+// 1 = raw key bytes 0-7, 2 = key bytes 8-9 and index.  Encoding order agrees
+// with byte order; equal encodings are split by the raw bytes, then by lo.
+__device__ __forceinline__ uint64_t sel_key(const Tile& t, uint32_t j, int sel) {
+  return sel == 0 ? t.E[j] : (sel == 1 ? t.A[j].hi : t.A[j].lo);
+}
 
 __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* wsum) {
   uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -73,11 +90,11 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* wsum) 
   return r;
 }
 
-// min and max of one key field over A[0, m)
-__device__ void block_minmax(const Pair* A, uint32_t m, bool use_lo, Misc& ms) {
+// block-wide min and max of one key field over the tile
+__device__ void block_minmax(const Tile& t, uint32_t m, int sel) {
   uint64_t mn = ~0ull, mx = 0;
   for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
-    uint64_t k = key_of(A[j], use_lo);
+    const uint64_t k = sel_key(t, j, sel);
     mn = min(mn, k);
     mx = max(mx, k);
   }
@@ -87,127 +104,198 @@ __device__ void block_minmax(const Pair* A, uint32_t m, bool use_lo, Misc& ms) {
   }
   const int warp = threadIdx.x >> 5;
   if ((threadIdx.x & 31) == 0) {
-    ms.red[0][warp] = mn;
-    ms.red[1][warp] = mx;
+    t.ms->red[0][warp] = mn;
+    t.ms->red[1][warp] = mx;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     uint64_t a = ~0ull, b = 0;
     for (int w = 0; w < kWarps; ++w) {
-      a = min(a, ms.red[0][w]);
-      b = max(b, ms.red[1][w]);
+      a = min(a, t.ms->red[0][w]);
+      b = max(b, t.ms->red[1][w]);
     }
-    ms.kmin = a;
-    ms.kmax = b;
+    t.ms->kmin = a;
+    t.ms->kmax = b;
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ bool idx_less(const Pair* A, uint32_t a, uint32_t b) {
-  if (a == kSent) return false;
-  if (b == kSent) return true;
-  return pair_less(A[a], A[b]);
+// insertion sort of perm[s, e) by the full key (the paper's touch-up)
+__device__ __forceinline__ void insertion_sort(const Tile& t, uint32_t s, uint32_t e) {
+  for (uint32_t i = s + 1; i < e; ++i) {
+    const uint16_t v = t.perm[i];
+    const Pair pv = t.A[v];
+    uint32_t k = i;
+    while (k > s && pair_less(pv, t.A[t.perm[k - 1]])) {
+      t.perm[k] = t.perm[k - 1];
+      --k;
+    }
+    t.perm[k] = v;
+  }
 }
 
-// Bitonic sort of `len` indices perm[start, start+len) by A[.], through scratch (pow2 >= len entries).
-__device__ void bitonic_run(const Pair* A, uint16_t* perm, uint32_t start, uint32_t len, uint32_t* scratch) {
-  uint32_t m2 = 1;
-  while (m2 < len) m2 <<= 1;
-  for (uint32_t i = threadIdx.x; i < m2; i += kThreads) scratch[i] = i < len ? perm[start + i] : kSent;
-  __syncthreads();
-  for (uint32_t k = 2; k <= m2; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < m2; i += kThreads) {
-        uint32_t ixj = i ^ j;
-        if (ixj > i) {
-          uint32_t a = scratch[i], b = scratch[ixj];
-          bool up = (i & k) == 0;
-          if (idx_less(A, b, a) == up) {
-            scratch[i] = b;
-            scratch[ixj] = a;
-          }
-        }
+__device__ __forceinline__ uint64_t warp_min(uint64_t v) {
+  for (int d = 16; d; d >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, d));
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_max(uint64_t v) {
+  for (int d = 16; d; d >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, d));
+  return v;
+}
+
+// One warp sorts perm[s0, s0+len0) completely: counting-sort refinement on a
+// digit of the run's own key range, recursively (explicit stack), with
+// insertion sort for short sub-runs.  Every pass splits a run into at least
+// two non-empty parts, so it terminates.
+__device__ void warp_refine(const Tile& t, uint32_t s0, uint32_t len0) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t* stk = t.stk + warp * t.stk_cap;
+  uint32_t* top = &t.ms->stk_top[warp];
+  if (lane == 0) {
+    stk[0] = (s0 << 16) | len0;
+    *top = 1;
+  }
+  __syncwarp();
+  for (;;) {
+    const uint32_t n_top = *top;
+    __syncwarp();
+    if (n_top == 0) break;
+    const uint32_t ent = stk[n_top - 1];
+    __syncwarp();
+    if (lane == 0) *top = n_top - 1;
+    __syncwarp();
+    const uint32_t s = ent >> 16, len = ent & 0xFFFFu;
+    int sel = 0;
+    uint64_t mn = ~0ull, mx = 0;
+    for (;;) {
+      mn = ~0ull;
+      mx = 0;
+      for (uint32_t i = lane; i < len; i += 32) {
+        const uint64_t k = sel_key(t, t.perm[s + i], sel);
+        mn = min(mn, k);
+        mx = max(mx, k);
       }
-      __syncthreads();
+      mn = warp_min(mn);
+      mx = warp_max(mx);
+      if (mn < mx || sel == 2) break;
+      ++sel;
     }
+    const uint32_t logD = 31 - __clz(len);  // len > kShortRun, so D >= 16
+    const uint32_t D = 1u << logD;
+    const uint64_t span = mx - mn;
+    const uint32_t bits = 64 - __clzll((long long)span);
+    const uint32_t shift = bits > logD ? bits - logD : 0;
+    for (uint32_t d = lane; d < D; d += 32) t.cnt[s + d] = 0;
+    __syncwarp();
+    for (uint32_t i = lane; i < len; i += 32)
+      atomicAdd(t.cnt + s + (uint32_t)((sel_key(t, t.perm[s + i], sel) - mn) >> shift), 1u);
+    __syncwarp();
+    {
+      const uint32_t per = (D + 31) / 32;
+      const uint32_t b = min(D, lane * per), e = min(D, b + per);
+      uint32_t local = 0;
+      for (uint32_t d = b; d < e; ++d) local += t.cnt[s + d];
+      uint32_t incl = local;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+      }
+      uint32_t run = s + incl - local;
+      for (uint32_t d = b; d < e; ++d) {
+        const uint32_t c = t.cnt[s + d];
+        t.cnt[s + d] = run;
+        run += c;
+      }
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < len; i += 32) {
+      const uint16_t j = t.perm[s + i];
+      const uint32_t pos = atomicAdd(t.cnt + s + (uint32_t)((sel_key(t, j, sel) - mn) >> shift), 1u);
+      t.perm2[pos] = j;
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < len; i += 32) t.perm[s + i] = t.perm2[s + i];
+    __syncwarp();
+    for (uint32_t d = lane; d < D; d += 32) {
+      const uint32_t ss = d ? t.cnt[s + d - 1] : s, ee = t.cnt[s + d];
+      const uint32_t l = ee - ss;
+      if (l >= 2 && l <= kShortRun) insertion_sort(t, ss, ee);
+      else if (l > kShortRun) stk[atomicAdd(top, 1u)] = (ss << 16) | l;
+    }
+    __syncwarp();
   }
-  for (uint32_t i = threadIdx.x; i < len; i += kThreads) perm[start + i] = (uint16_t)scratch[i];
-  __syncthreads();
 }
 
-// Sort A[0, m) (m <= cap) in shared memory: on return perm[0, m) lists A in
-// (hi, lo) order.  cnt has room for cap counters.
-__device__ void tile_sort(const Pair* A, uint32_t m, uint32_t* cnt, uint16_t* perm, Misc& ms) {
+// Sort the tile A[0, m) (m <= cap; E filled): on return perm[0, m) lists A in
+// (hi, lo) order.  First digit pass block-wide over the whole tile, then the
+// long runs are refined by warps in parallel.
+__device__ void tile_sort(const Tile& t, uint32_t m) {
+  Misc& ms = *t.ms;
   if (m <= 1) {
-    if (threadIdx.x == 0 && m == 1) perm[0] = 0;
+    if (threadIdx.x == 0 && m == 1) t.perm[0] = 0;
     __syncthreads();
     return;
   }
-  block_minmax(A, m, false, ms);
-  bool use_lo = ms.kmin == ms.kmax;
-  if (use_lo) block_minmax(A, m, true, ms);
+  int sel = 0;
+  block_minmax(t, m, 0);
+  if (ms.kmin == ms.kmax) {
+    sel = 1;
+    block_minmax(t, m, 1);
+    if (ms.kmin == ms.kmax) {
+      sel = 2;
+      block_minmax(t, m, 2);
+    }
+  }
   const uint64_t kmin = ms.kmin, span = ms.kmax - ms.kmin;
   uint32_t logD = 0;
   while ((1u << logD) < m) ++logD;
   const uint32_t D = 1u << logD;
   const uint32_t bits = span ? 64 - __clzll((long long)span) : 0;
   const uint32_t shift = bits > logD ? bits - logD : 0;
-  for (uint32_t d = threadIdx.x; d < D; d += kThreads) cnt[d] = 0;
-  if (threadIdx.x == 0) ms.nlong = 0;
+  for (uint32_t d = threadIdx.x; d < D; d += kThreads) t.cnt[d] = 0;
+  if (threadIdx.x == 0) {
+    ms.nlong = 0;
+    ms.next_long = 0;
+  }
   __syncthreads();
   for (uint32_t j = threadIdx.x; j < m; j += kThreads)
-    atomicAdd(cnt + ((key_of(A[j], use_lo) - kmin) >> shift), 1u);
+    atomicAdd(t.cnt + (uint32_t)((sel_key(t, j, sel) - kmin) >> shift), 1u);
   __syncthreads();
-  // exclusive scan of the D digit counters, D/kThreads per thread
   {
     const uint32_t per = (D + kThreads - 1) / kThreads;
     const uint32_t b = min(D, threadIdx.x * per), e = min(D, b + per);
     uint32_t local = 0;
-    for (uint32_t d = b; d < e; ++d) local += cnt[d];
+    for (uint32_t d = b; d < e; ++d) local += t.cnt[d];
     uint32_t run = block_scan_excl(local, ms.wsum);
     for (uint32_t d = b; d < e; ++d) {
-      uint32_t c = cnt[d];
-      cnt[d] = run;
+      const uint32_t c = t.cnt[d];
+      t.cnt[d] = run;
       run += c;
     }
   }
   __syncthreads();
   for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
-    uint32_t pos = atomicAdd(cnt + ((key_of(A[j], use_lo) - kmin) >> shift), 1u);
-    perm[pos] = (uint16_t)j;
+    const uint32_t pos = atomicAdd(t.cnt + (uint32_t)((sel_key(t, j, sel) - kmin) >> shift), 1u);
+    t.perm[pos] = (uint16_t)j;
   }
   __syncthreads();
-  // touch-up: cnt[d] is now the end of run d
   for (uint32_t d = threadIdx.x; d < D; d += kThreads) {
-    const uint32_t s = d ? cnt[d - 1] : 0, e = cnt[d];
+    const uint32_t s = d ? t.cnt[d - 1] : 0, e = t.cnt[d];
     const uint32_t len = e - s;
-    if (len < 2) continue;
-    if (len <= 32) {
-      for (uint32_t i = s + 1; i < e; ++i) {
-        uint16_t v = perm[i];
-        const Pair pv = A[v];
-        uint32_t k = i;
-        while (k > s && pair_less(pv, A[perm[k - 1]])) {
-          perm[k] = perm[k - 1];
-          --k;
-        }
-        perm[k] = v;
-      }
-    } else {
-      uint32_t slot = atomicAdd(&ms.nlong, 1u);
-      if (slot < (uint32_t)kLongMax) {
-        ms.long_start[slot] = s;
-        ms.long_len[slot] = len;
-      }
-    }
+    if (len >= 2 && len <= kShortRun) insertion_sort(t, s, e);
+    else if (len > kShortRun) t.longs[atomicAdd(&ms.nlong, 1u)] = (s << 16) | len;
   }
   __syncthreads();
-  const uint32_t nlong = ms.nlong;
-  if (nlong > (uint32_t)kLongMax) {
-    bitonic_run(A, perm, 0, m, cnt);  // too many long runs: one network over the whole tile
-  } else {
-    for (uint32_t r = 0; r < nlong; ++r) bitonic_run(A, perm, ms.long_start[r], ms.long_len[r], cnt);
+  const uint32_t lane = threadIdx.x & 31;
+  for (;;) {
+    uint32_t r = 0;
+    if (lane == 0) r = atomicAdd(&ms.next_long, 1u);
+    r = __shfl_sync(0xffffffffu, r, 0);
+    if (r >= ms.nlong) break;
+    const uint32_t ent = t.longs[r];
+    warp_refine(t, ent >> 16, ent & 0xFFFFu);
   }
+  __syncthreads();
 }
 
 // Gather m records in sorted order into out[o0, o0 + m): warp-cooperative,
@@ -250,22 +338,30 @@ __device__ __forceinline__ uint32_t merge_split(const Pair* a, uint32_t na, cons
   return lo;
 }
 
+__device__ __forceinline__ void load_tile(const Tile& t, const Pair* src, uint32_t m) {
+  for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
+    const Pair p = src[j];
+    t.A[j] = p;
+    t.E[j] = enc9_pair(p);
+  }
+  __syncthreads();
+}
+
 // items above cap: sort cap-sized chunks in place, then merge passes between
 // pairs and temp; returns the array holding the sorted run
-__device__ const Pair* sort_oversize(const KArgs& k, uint64_t o0, uint32_t m, Pair* A, uint32_t* cnt, uint16_t* perm,
-                                     Misc& ms) {
+__device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0, uint32_t m) {
   const uint32_t cap = k.cap;
   Pair* src = k.pairs;
   Pair* dst = k.temp;
+  Misc& ms = *t.ms;
   for (uint32_t c0 = 0; c0 < m; c0 += cap) {
     const uint32_t mc = min(cap, m - c0);
-    for (uint32_t j = threadIdx.x; j < mc; j += kThreads) A[j] = src[o0 + c0 + j];
-    __syncthreads();
-    tile_sort(A, mc, cnt, perm, ms);
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < mc; j += kThreads) src[o0 + c0 + j] = A[perm[j]];
+    load_tile(t, src + o0 + c0, mc);
+    tile_sort(t, mc);
+    for (uint32_t j = threadIdx.x; j < mc; j += kThreads) src[o0 + c0 + j] = t.A[t.perm[j]];
     __syncthreads();
   }
+  Pair* A = t.A;
   for (uint32_t w = cap; w < m; w *= 2) {
     for (uint32_t t0 = 0; t0 < m; t0 += cap) {
       const uint32_t p0 = (t0 / (2 * w)) * (2 * w);
@@ -292,9 +388,9 @@ __device__ const Pair* sort_oversize(const KArgs& k, uint64_t o0, uint32_t m, Pa
           else hi = mid;
         }
         uint32_t ia = lo, ib = d - lo;
-        for (uint32_t t = 0; t < per && d + t < tot; ++t) {
+        for (uint32_t q = 0; q < per && d + q < tot; ++q) {
           bool takeA = ib >= nb || (ia < na && !pair_less(A[na + ib], A[ia]));
-          dst[o0 + t0 + d + t] = takeA ? A[ia++] : A[na + ib++];
+          dst[o0 + t0 + d + q] = takeA ? A[ia++] : A[na + ib++];
         }
       }
       __syncthreads();
@@ -307,29 +403,48 @@ __device__ const Pair* sort_oversize(const KArgs& k, uint64_t o0, uint32_t m, Pa
   return src;
 }
 
-__device__ void process_item(const KArgs& k, uint32_t it, Pair* A, uint32_t* cnt, uint16_t* perm, Misc& ms) {
+__device__ void process_item(const KArgs& k, const Tile& t, uint32_t it) {
   const uint64_t o0 = k.bin_off[k.items[it]];
   const uint32_t m = k.bin_off[k.items[it + 1]] - (uint32_t)o0;
   if (m == 0) return;
   if (m <= k.cap) {
-    for (uint32_t j = threadIdx.x; j < m; j += kThreads) A[j] = k.pairs[o0 + j];
-    __syncthreads();
-    tile_sort(A, m, cnt, perm, ms);
-    __syncthreads();
-    gather(k.in, k.out, o0, m, [&](uint32_t j) { return (uint32_t)A[perm[j]].lo; });
+    load_tile(t, k.pairs + o0, m);
+    tile_sort(t, m);
+    gather(k.in, k.out, o0, m, [&](uint32_t j) { return (uint32_t)t.A[t.perm[j]].lo; });
   } else {
-    const Pair* sorted = sort_oversize(k, o0, m, A, cnt, perm, ms);
+    const Pair* sorted = sort_oversize(k, t, o0, m);
     gather(k.in, k.out, o0, m, [&](uint32_t j) { return (uint32_t)sorted[o0 + j].lo; });
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kThreads) sort_gather_kernel(KArgs k) {
+__device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
+  Tile t;
+  uint8_t* p = smem;
+  t.A = reinterpret_cast<Pair*>(p);
+  p += (size_t)cap * sizeof(Pair);
+  t.E = reinterpret_cast<uint64_t*>(p);
+  p += (size_t)cap * 8;
+  t.cnt = reinterpret_cast<uint32_t*>(p);
+  p += (size_t)cap * 4;
+  t.perm = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * 2;
+  t.perm2 = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * 2;
+  t.stk_cap = cap / 16 + 1;
+  t.longs = reinterpret_cast<uint32_t*>(p);
+  p += (size_t)t.stk_cap * 4;
+  t.stk = reinterpret_cast<uint32_t*>(p);
+  p += (size_t)kWarps * t.stk_cap * 4;
+  p = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+  t.ms = reinterpret_cast<Misc*>(p);
+  return t;
+}
+
+__global__ void __launch_bounds__(kThreads, 3) sort_gather_kernel(KArgs k) {
   extern __shared__ __align__(16) uint8_t smem[];
-  Pair* A = reinterpret_cast<Pair*>(smem);
-  uint32_t* cnt = reinterpret_cast<uint32_t*>(smem + (size_t)k.cap * sizeof(Pair));
-  uint16_t* perm = reinterpret_cast<uint16_t*>(smem + (size_t)k.cap * (sizeof(Pair) + 4));
-  Misc& ms = *reinterpret_cast<Misc*>(smem + (size_t)k.cap * (sizeof(Pair) + 6));
+  const Tile t = carve(smem, k.cap);
+  Misc& ms = *t.ms;
   const uint32_t num_items = k.ctrl[kNumItems];
   if (k.persistent) {
     const uint32_t num_over = k.ctrl[kNumOversize];
@@ -346,11 +461,11 @@ __global__ void __launch_bounds__(kThreads) sort_gather_kernel(KArgs k) {
         it = j - num_over;
         if (k.bin_off[k.items[it + 1]] - k.bin_off[k.items[it]] > k.cap) continue;  // done in the oversize phase
       }
-      process_item(k, it, A, cnt, perm, ms);
+      process_item(k, t, it);
     }
   } else {
     const uint32_t i0 = k.part_items[k.part], i1 = k.part_items[k.part + 1];
-    for (uint32_t it = i0 + blockIdx.x; it < i1; it += gridDim.x) process_item(k, it, A, cnt, perm, ms);
+    for (uint32_t it = i0 + blockIdx.x; it < i1; it += gridDim.x) process_item(k, t, it);
   }
 }
 
@@ -364,7 +479,10 @@ __global__ void part_items_kernel(const uint32_t* cuts, const uint32_t* item_of_
 
 }  // namespace
 
-size_t sort_smem_bytes(uint32_t cap) { return (size_t)cap * (sizeof(Pair) + 6) + sizeof(Misc) + 16; }
+size_t sort_smem_bytes(uint32_t cap) {
+  const size_t stk = (size_t)(cap / 16 + 1) * 4;
+  return (size_t)cap * (sizeof(Pair) + 8 + 4 + 2 + 2) + stk * (1 + kWarps) + 16 + sizeof(Misc);
+}
 
 cudaError_t sort_items(const SortArgs& a) {
   KArgs k = {};

@@ -24,7 +24,7 @@ def test_noalloc_equals_workspace_sort_twice():
     L = elsar.lib()
     p = elsar.Params(num_partitions=256, seed=11)
     n = 300_000
-    assert elsar.workspace_size(n, p) <= (16 << 20)
+    assert elsar.workspace_size(n, p) <= (16 << 20), elsar.workspace_size(n, p)
     sets = [recgen.KeySpec("zipf", s=1.3, dup=0.10, seed=21), recgen.KeySpec("uniform", seed=22)]
     for spec in sets:
         d_in = torch.from_numpy(recgen.generate_cpu(n, spec)).cuda()
