@@ -154,29 +154,33 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* e
   return total;
 }
 
-// Single CTA: bin offsets (exclusive scan of the histogram), scatter cursors, max bin.
+// Single CTA: bin offsets (exclusive scan of the histogram), scatter cursors,
+// max bin.  Coalesced tiles of kScanThreads bins with a running carry.
 __global__ void __launch_bounds__(kScanThreads) scan_bins(const uint32_t* hist, uint32_t log2B,
                                                           uint32_t* __restrict__ bin_off, uint32_t* cursor,
                                                           uint32_t* ctrl) {
   __shared__ uint32_t wsum[33];
+  __shared__ uint32_t carry_sh;
   const uint32_t B = 1u << log2B;
-  const uint32_t per = (B + kScanThreads - 1) / kScanThreads;
-  const uint32_t b = min(B, threadIdx.x * per), e = min(B, b + per);
-  uint32_t local = 0, mx = 0;
-  for (uint32_t q = b; q < e; ++q) {
-    uint32_t h = hist[q];
-    local += h;
+  if (threadIdx.x == 0) carry_sh = 0;
+  uint32_t mx = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < B; base += kScanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    const uint32_t h = q < B ? hist[q] : 0;  // hist and cursor may be the same array
     mx = max(mx, h);
+    uint32_t excl;
+    const uint32_t tot = block_exclusive_scan(h, &excl, wsum);
+    const uint32_t carry = carry_sh;
+    if (q < B) {
+      bin_off[q] = carry + excl;
+      cursor[q] = carry + excl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_sh = carry + tot;
+    __syncthreads();
   }
-  uint32_t run;
-  uint32_t total = block_exclusive_scan(local, &run, wsum);
-  for (uint32_t q = b; q < e; ++q) {
-    const uint32_t h = hist[q];  // hist and cursor may be the same array
-    bin_off[q] = run;
-    cursor[q] = run;
-    run += h;
-  }
-  if (threadIdx.x == 0) bin_off[B] = total;
+  if (threadIdx.x == 0) bin_off[B] = carry_sh;
   for (int d = 16; d; d >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
   if ((threadIdx.x & 31) == 0) atomicMax(ctrl + kMaxBin, mx);
 }
@@ -229,41 +233,47 @@ __global__ void cuts_kernel(const uint32_t* __restrict__ bin_off, uint32_t log2B
 // item if it starts a partition, is not "small" (> W = cap/2 pairs), follows a
 // bin that is not small, or its start offset enters a new W-window; a run of
 // small bins inside one window holds < 2W = cap pairs.  Oversize bins
-// (> cap pairs) are listed separately.
+// (> cap pairs) are listed separately.  item_flag becomes the item id of
+// every bin.  Coalesced tiles with a running carry.
 __global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __restrict__ bin_off, uint32_t log2B,
                                                              uint32_t cap, uint32_t* item_flag, uint32_t* items,
                                                              uint32_t* oversize, uint32_t* ctrl) {
   __shared__ uint32_t wsum[33];
+  __shared__ uint32_t carry_sh;
   const uint32_t B = 1u << log2B;
   const uint32_t W = cap / 2;
-  const uint32_t per = (B + kScanThreads - 1) / kScanThreads;
-  const uint32_t b = min(B, threadIdx.x * per), e = min(B, b + per);
-  uint32_t local = 0;
-  for (uint32_t q = b; q < e; ++q) {
-    const uint32_t cnt = bin_off[q + 1] - bin_off[q];
-    bool f = item_flag[q] != 0 || q == 0 || cnt > W;
-    if (!f) {
-      const uint32_t pc = bin_off[q] - bin_off[q - 1];
-      f = pc > W || (bin_off[q] / W) != (bin_off[q - 1] / W);
+  if (threadIdx.x == 0) carry_sh = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < B; base += kScanThreads) {
+    const uint32_t q = base + threadIdx.x;
+    uint32_t f = 0;
+    if (q < B) {
+      const uint32_t o = bin_off[q], cnt = bin_off[q + 1] - o;
+      f = item_flag[q] != 0 || q == 0 || cnt > W;
+      if (!f) {
+        const uint32_t po = bin_off[q - 1];
+        f = (o - po) > W || (o / W) != (po / W);
+      }
     }
-    item_flag[q] = f;
-    local += f;
-  }
-  uint32_t run;
-  uint32_t total = block_exclusive_scan(local, &run, wsum);
-  for (uint32_t q = b; q < e; ++q) {
-    if (item_flag[q]) {
-      items[run] = q;
-      if (bin_off[q + 1] - bin_off[q] > cap) oversize[atomicAdd(ctrl + kNumOversize, 1u)] = run;
-      item_flag[q] = run;
-      ++run;
-    } else {
-      item_flag[q] = run - 1;  // item id of every bin
+    uint32_t excl;
+    const uint32_t tot = block_exclusive_scan(f, &excl, wsum);
+    const uint32_t id = carry_sh + excl;
+    if (q < B) {
+      if (f) {
+        items[id] = q;
+        if (bin_off[q + 1] - bin_off[q] > cap) oversize[atomicAdd(ctrl + kNumOversize, 1u)] = id;
+        item_flag[q] = id;
+      } else {
+        item_flag[q] = id - 1;
+      }
     }
+    __syncthreads();
+    if (threadIdx.x == 0) carry_sh += tot;
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
-    items[total] = B;
-    ctrl[kNumItems] = total;
+    items[carry_sh] = B;
+    ctrl[kNumItems] = carry_sh;
   }
 }
 

@@ -298,8 +298,12 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
   __syncthreads();
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Gather m records in sorted order into out[o0, o0 + m): warp-cooperative,
-// 32 records (800 words) per step, loads and stores both coalesced.
+// 32 records (800 words) per step, loads and stores both coalesced.  While a
+// warp loads one group it asks L2 for the lines of its next group, so twice as
+// many records are in flight without holding more registers.
 template <typename IdxFn>
 __device__ __forceinline__ void gather(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, uint64_t o0,
                                        uint32_t m, IdxFn idx_of) {
@@ -309,6 +313,12 @@ __device__ __forceinline__ void gather(const uint8_t* __restrict__ in, uint8_t* 
   for (uint32_t j0 = warp * 32; j0 < m; j0 += kThreads) {
     const uint32_t nrec = min(32u, m - j0);
     const uint32_t my = lane < nrec ? idx_of(j0 + lane) : 0;
+    const uint32_t jn = j0 + kThreads + lane;
+    if (jn < m) {
+      const uint8_t* r = in + (uint64_t)idx_of(jn) * kRecord;
+      prefetch_l2(r);
+      prefetch_l2(r + kRecord - 1);
+    }
     uint32_t v[25];
 #pragma unroll
     for (int it = 0; it < 25; ++it) {
@@ -403,10 +413,16 @@ __device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0,
   return src;
 }
 
-__device__ void process_item(const KArgs& k, const Tile& t, uint32_t it) {
+__device__ void process_item(const KArgs& k, const Tile& t, uint32_t it, uint32_t num_items) {
   const uint64_t o0 = k.bin_off[k.items[it]];
   const uint32_t m = k.bin_off[k.items[it + 1]] - (uint32_t)o0;
   if (m == 0) return;
+  if (threadIdx.x == 0 && it + gridDim.x < num_items) {
+    // the pairs of the item this CTA will most likely take next: into L2 now
+    const uint32_t nx = it + gridDim.x;
+    const uint64_t a = k.bin_off[k.items[nx]], b = k.bin_off[k.items[nx + 1]];
+    for (uint64_t q = a * sizeof(Pair); q < b * sizeof(Pair); q += 128) prefetch_l2(reinterpret_cast<const uint8_t*>(k.pairs) + q);
+  }
   if (m <= k.cap) {
     load_tile(t, k.pairs + o0, m);
     tile_sort(t, m);
@@ -461,11 +477,11 @@ __global__ void __launch_bounds__(kThreads, 3) sort_gather_kernel(KArgs k) {
         it = j - num_over;
         if (k.bin_off[k.items[it + 1]] - k.bin_off[k.items[it]] > k.cap) continue;  // done in the oversize phase
       }
-      process_item(k, t, it);
+      process_item(k, t, it, num_items);
     }
   } else {
     const uint32_t i0 = k.part_items[k.part], i1 = k.part_items[k.part + 1];
-    for (uint32_t it = i0 + blockIdx.x; it < i1; it += gridDim.x) process_item(k, t, it);
+    for (uint32_t it = i0 + blockIdx.x; it < i1; it += gridDim.x) process_item(k, t, it, 0);
   }
 }
 
