@@ -33,13 +33,21 @@ RECORD = 100
 # pair, read the 100-byte record, write it to its place in the output
 SORT_GATHER_BYTES = 16 + 100 + 100
 CPU_SAMPLE = 10_000_000  # records of each key set sorted by the oracle for the CPU baseline
+# DRAM bytes per record of sort_gather_kernel (dram__bytes_read.sum + dram__bytes_write.sum
+# of one ncu launch divided by its records), from the capture summarised in
+# profiles/sort_gather_kernel_uniform_20M.md; None once the kernel changes.
+SORT_GATHER_TRAFFIC_PER_RECORD = None
 METRIC = "GB/s sorted (100-B recs), learned+batched vs plain on 1 B300; % HBM roofline"
+
+
+_SETS = ("uniform", "zipf")
 
 
 def workloads():
     import recgen
 
-    return [recgen.UNIFORM_100M, recgen.ZIPF11_100M]
+    table = {"uniform": recgen.UNIFORM_100M, "zipf": recgen.ZIPF11_100M}
+    return [table[s] for s in _SETS]
 
 
 def workload_config(extra=None):
@@ -125,7 +133,7 @@ def cpu_baseline(args, world_rank=0):
 
     tot_bytes, tot_s = 0, 0.0
     for wl in workloads():
-        host = recgen.generate_cpu(N_RECORDS, wl["spec"], i0=0, count=CPU_SAMPLE)
+        host = recgen.generate_cpu(wl["n"], wl["spec"], i0=0, count=CPU_SAMPLE)
         log2B = oracle.default_fine_log2(CPU_SAMPLE, PARTITIONS)
         t0 = time.perf_counter()
         oracle.sort(host, PARTITIONS, log2B, S=oracle.default_sample_size(CPU_SAMPLE), seed=0x5EED, balance=1)
@@ -198,7 +206,7 @@ def run_elsar(args):
     p = elsar.Params(num_partitions=PARTITIONS, seed=0x5EED, tile_pairs=args.tile_pairs)
     p_plain = elsar.Params(num_partitions=PARTITIONS, seed=0x5EED, balance=elsar.BALANCE_PAPER,
                            schedule=elsar.SCHED_PER_PARTITION, tile_pairs=args.tile_pairs)
-    n = N_RECORDS
+    n = args.records
     ins = []
     for wl in workloads():
         d = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
@@ -240,21 +248,24 @@ def run_elsar(args):
     achieved = n * SORT_GATHER_BYTES / (sg_ms / 1e3) / 1e9
     roof = {"kernel": "sort_gather_kernel", "bound": "hbm", "achieved": round(achieved, 1),
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
-            "peak_source": how, "traffic": args.traffic,
+            "peak_source": how,
+            "traffic": round(SORT_GATHER_TRAFFIC_PER_RECORD * n) if SORT_GATHER_TRAFFIC_PER_RECORD else None,
             "bytes_per_record": SORT_GATHER_BYTES, "avg_launch_ms": round(sg_ms, 3)}
 
     # plain form on the same data
-    for _ in range(args.warmup):
+    plain = None
+    for _ in range(args.warmup if not args.no_plain else 0):
         step(p_plain, stats=False)
     torch.cuda.synchronize()
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step(p_plain, stats=False)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = ev0.elapsed_time(ev1) / args.steps
-    plain = {"value": round(bytes_per_step / (plain_ms / 1e3) / 1e9, 2), "ms_per_step": round(plain_ms, 3),
-             "form": "paper partition rule, one sort launch per partition"}
+    if not args.no_plain:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(p_plain, stats=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = ev0.elapsed_time(ev1) / args.steps
+        plain = {"value": round(bytes_per_step / (plain_ms / 1e3) / 1e9, 2), "ms_per_step": round(plain_ms, 3),
+                 "form": "paper partition rule, one sort launch per partition"}
 
     # end to end through elsar_sort_host: pinned host in -> device -> sorted -> pinned host out
     e2e = None
@@ -283,7 +294,8 @@ def run_elsar(args):
         "metric": METRIC,
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u64", "data": "synthetic", "config": workload_config({"tile_pairs": args.tile_pairs or 4096}),
+        "dtype": "u64", "data": "synthetic", "config": workload_config({"tile_pairs": args.tile_pairs or 2048, "n_records_per_set": n,
+                                   "sets": len(workloads())}),
         "records_per_s": round(world * len(workloads()) * n / (ms / 1e3)),
         "hbm_frac_200B": round(world * len(workloads()) * n * 200 / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "plain": plain,
@@ -307,9 +319,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--traffic", type=float, default=None,
-                    help="ncu dram bytes per launch of the sort kernel (from the committed profile)")
+    ap.add_argument("--records", type=int, default=N_RECORDS, help="records per key set (profiling cases use fewer)")
+    ap.add_argument("--sets", default="uniform,zipf", help="key sets to sort per step")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     args = ap.parse_args()
+    global _SETS
+    _SETS = tuple(args.sets.split(","))
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -90,6 +90,10 @@ typedef struct elsar_stats {
   uint32_t model_nodes; /* RMI nodes */
   uint64_t max_partition;
   uint64_t max_bin;
+  uint32_t model_used;      /* elsar_model_kind that classified the records */
+  uint32_t fallback_reason; /* MLP asked for but not used: 1 boundary check (F of the smallest / largest
+                               sample key not within 1/16 of 0 / 1), 2 less balanced than the RMI on a
+                               held-out sample, 3 full-data partition imbalance above 1.1; 0 otherwise */
 } elsar_stats;
 
 /* Fill *p with the defaults. */
@@ -162,6 +166,34 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
  */
 elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_in,
                              void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
+
+/*
+ * The learned CDF network (model_kind = ELSAR_MODEL_MLP) on its own, for
+ * inspection and parity checks.  It is not in the paper, whose model
+ * (Sec. 3.1) is the RMI; its definition: 12 features of a key encoding x are
+ * ramps between 13 sorted-sample knots T (phi_m = clamp(x - T_m, 0, W_m) / W_m
+ * with W_m = T_{m+1} - T_m, formed exactly then scaled in FP64 and rounded to
+ * FP32), two hidden layers of 32 with sigma(z) = 0.5 + 0.5 z / (1 + |z|),
+ * F = clamp(output, 0, 1); weights are non-negative.  Parameters are 1505
+ * floats laid out W1[32][12], b1[32], W2[32][32], b2[32], w3[32], b3.
+ *
+ * elsar_mlp_eval: F of each key encoding, FP32 (d_w 1505 floats, d_knots 13
+ *   u64, d_x n u64 encodings, d_F n floats).  Asynchronous.
+ * elsar_mlp_grad: gradient of mean((F - y)^2) over n samples, FP32 with a
+ *   fixed summation order (d_y n floats, d_grad 1505 floats); needs
+ *   elsar_mlp_grad_workspace(n) bytes of scratch.  Asynchronous.
+ * elsar_mlp_splitters: the 2^log2B fine-bin splitters of the network
+ *   (t[0] = 0; t[q] = smallest encoding whose bin floor(2^log2B F) >= q, then
+ *   made non-decreasing).  Asynchronous.
+ * Errors: EINVAL for null pointers or n >= 2^32; ECUDA.
+ */
+size_t elsar_mlp_grad_workspace(uint64_t n);
+elsar_status elsar_mlp_eval(const float* d_w, const uint64_t* d_knots, const uint64_t* d_x, uint64_t n, float* d_F,
+                            elsar_stream_t stream);
+elsar_status elsar_mlp_grad(const float* d_w, const uint64_t* d_knots, const uint64_t* d_x, const float* d_y,
+                            uint64_t n, float* d_grad, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
+elsar_status elsar_mlp_splitters(const float* d_w, const uint64_t* d_knots, uint32_t log2B, uint64_t* d_t,
+                                 elsar_stream_t stream);
 
 /* Bytes of the scratch area built into the library for elsar_sort_noalloc. */
 #define ELSAR_NOALLOC_SCRATCH_BYTES (16u << 20)

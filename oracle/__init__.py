@@ -14,7 +14,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = os.path.join(_HERE, "libelsar_oracle.so")
-_SRCS = ["elsar_oracle.cpp"]
+_SRCS = ["elsar_oracle.cpp", "mlp_oracle.cpp"]
 RECORD = 100
 
 _lib = None
@@ -51,6 +51,16 @@ def lib():
             "eo_sort": (I32, [P, U64, U32, U32, U32, U32, U64, U64, I32, P, P, P, P, P, P]),
             "eo_classify": (I32, [P, U64, U32, U32, U32, U32, U64, U64, I32, P, P]),
             "eo_stable_sort": (None, [P, U64, P]),
+            "eo_mlp_params": (I32, []),
+            "eo_mlp_knots": (None, [P, U64, P]),
+            "eo_mlp_init": (None, [P]),
+            "eo_mlp_features": (None, [P, P, U64, P]),
+            "eo_mlp_forward32": (None, [P, P, U64, P]),
+            "eo_mlp_forward64": (None, [P, P, U64, P]),
+            "eo_mlp_grad64": (None, [P, P, P, U64, P]),
+            "eo_mlp_train64": (None, [P, P, P, U64, U32, U32, ctypes.c_double, P]),
+            "eo_mlp_splitters": (None, [P, P, U32, P]),
+            "eo_bins_by_splitters": (None, [P, U32, P, U64, P]),
             "eo_validate": (I32, [P, P, U64]),
         }
         for name, (res, args) in sig.items():
@@ -186,3 +196,79 @@ def stable_sort(recs: np.ndarray) -> np.ndarray:
 
 def validate(inp: np.ndarray, out: np.ndarray) -> int:
     return int(lib().eo_validate(_ptr(inp), _ptr(out), inp.size // RECORD))
+
+
+# ---------------------------------------------------------------- monotone MLP CDF (mlp_oracle.cpp)
+MLP_FEATURES, MLP_HIDDEN = 12, 32
+MLP_PARAMS = 12 * 32 + 32 + 32 * 32 + 32 + 32 + 1  # 1505
+MLP_SLICES = {"W1": (0, 384), "b1": (384, 416), "W2": (416, 1440), "b2": (1440, 1472), "w3": (1472, 1504),
+              "b3": (1504, 1505)}
+
+
+def mlp_knots(sorted_sample: np.ndarray) -> np.ndarray:
+    s = np.ascontiguousarray(sorted_sample, dtype=np.uint64)
+    T = np.empty(13, dtype=np.uint64)
+    lib().eo_mlp_knots(_ptr(s), s.size, _ptr(T))
+    return T
+
+
+def mlp_init() -> np.ndarray:
+    w = np.empty(MLP_PARAMS, dtype=np.float32)
+    lib().eo_mlp_init(_ptr(w))
+    return w
+
+
+def mlp_features(T: np.ndarray, xs: np.ndarray) -> np.ndarray:
+    xs = np.ascontiguousarray(xs, dtype=np.uint64)
+    phi = np.empty((xs.size, 12), dtype=np.float32)
+    lib().eo_mlp_features(_ptr(np.ascontiguousarray(T, dtype=np.uint64)), _ptr(xs), xs.size, _ptr(phi))
+    return phi
+
+
+def mlp_forward32(w: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    phi = np.ascontiguousarray(phi, dtype=np.float32)
+    F = np.empty(phi.shape[0], dtype=np.float32)
+    lib().eo_mlp_forward32(_ptr(w), _ptr(phi), phi.shape[0], _ptr(F))
+    return F
+
+
+def mlp_forward64(w: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    F = np.empty(phi.shape[0])
+    lib().eo_mlp_forward64(_ptr(w), _ptr(phi), phi.shape[0], _ptr(F))
+    return F
+
+
+def mlp_grad64(w: np.ndarray, phi: np.ndarray, y: np.ndarray) -> np.ndarray:
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    g = np.empty(MLP_PARAMS)
+    lib().eo_mlp_grad64(_ptr(w), _ptr(phi), _ptr(y), y.size, _ptr(g))
+    return g
+
+
+def mlp_train64(w0: np.ndarray, phi: np.ndarray, y: np.ndarray, batch: int = 65536, epochs: int = 20,
+                lr: float = 1e-3):
+    w = np.array(w0, dtype=np.float64)
+    phi = np.ascontiguousarray(phi, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    loss = ctypes.c_double(0)
+    lib().eo_mlp_train64(_ptr(w), _ptr(phi), _ptr(y), y.size, batch, epochs, lr, ctypes.byref(loss))
+    return w, loss.value
+
+
+def mlp_splitters(w: np.ndarray, T: np.ndarray, log2B: int) -> np.ndarray:
+    t = np.empty(1 << log2B, dtype=np.uint64)
+    lib().eo_mlp_splitters(_ptr(np.ascontiguousarray(w, dtype=np.float32)),
+                           _ptr(np.ascontiguousarray(T, dtype=np.uint64)), log2B, _ptr(t))
+    return t
+
+
+def bins_by_splitters(t: np.ndarray, log2B: int, xs: np.ndarray) -> np.ndarray:
+    xs = np.ascontiguousarray(xs, dtype=np.uint64)
+    q = np.empty(xs.size, dtype=np.uint32)
+    lib().eo_bins_by_splitters(_ptr(np.ascontiguousarray(t, dtype=np.uint64)), log2B, _ptr(xs), xs.size, _ptr(q))
+    return q

@@ -37,7 +37,8 @@ class _Params(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("pass_ms", ctypes.c_float * 8), ("launches", ctypes.c_uint32), ("num_items", ctypes.c_uint32),
                 ("oversize_items", ctypes.c_uint32), ("model_nodes", ctypes.c_uint32),
-                ("max_partition", ctypes.c_uint64), ("max_bin", ctypes.c_uint64)]
+                ("max_partition", ctypes.c_uint64), ("max_bin", ctypes.c_uint64), ("model_used", ctypes.c_uint32),
+                ("fallback_reason", ctypes.c_uint32)]
 
 
 @dataclass
@@ -81,6 +82,10 @@ def lib():
             "elsar_sort": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_Stats)]),
             "elsar_sort_host": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
             "elsar_sort_noalloc": (ctypes.c_int, [P, P, U64, PP, P]),
+            "elsar_mlp_grad_workspace": (SZ, [U64]),
+            "elsar_mlp_eval": (ctypes.c_int, [P, P, P, U64, P, P]),
+            "elsar_mlp_grad": (ctypes.c_int, [P, P, P, P, U64, P, P, SZ, P]),
+            "elsar_mlp_splitters": (ctypes.c_int, [P, P, ctypes.c_uint32, P, P]),
             "elsar_status_str": (ctypes.c_char_p, [ctypes.c_int]),
             "elsar_last_error": (ctypes.c_char_p, []),
         }
@@ -171,7 +176,7 @@ def sort(d_in, d_out, n: int, p: Params | None = None, ws=None, stream=None, sta
         return None
     return dict(pass_ms=list(st.pass_ms)[:5], launches=st.launches, num_items=st.num_items,
                 oversize_items=st.oversize_items, model_nodes=st.model_nodes, max_partition=st.max_partition,
-                max_bin=st.max_bin)
+                max_bin=st.max_bin, model_used=st.model_used, fallback_reason=st.fallback_reason)
 
 
 def sort_noalloc(d_in, d_out, n: int, p: Params | None = None, stream=None):
@@ -183,6 +188,22 @@ def sort_host(h_in, h_out, n: int, p: Params, d_in, d_out, ws, stream=None):
     """Host records in (pinned for async DMA), host records out; synchronises."""
     _check(lib().elsar_sort_host(_ptr(h_in), _ptr(h_out), n, ctypes.byref(p.c()), _ptr(d_in), _ptr(d_out), _ptr(ws),
                                  _nbytes(ws), _stream(stream)))
+
+
+def mlp_eval(d_w, d_knots, d_x, n: int, d_F, stream=None):
+    _check(lib().elsar_mlp_eval(_ptr(d_w), _ptr(d_knots), _ptr(d_x), n, _ptr(d_F), _stream(stream)))
+
+
+def mlp_grad(d_w, d_knots, d_x, d_y, n: int, d_grad, stream=None):
+    import torch
+
+    ws = torch.empty(lib().elsar_mlp_grad_workspace(n), dtype=torch.uint8, device=d_w.device)
+    _check(lib().elsar_mlp_grad(_ptr(d_w), _ptr(d_knots), _ptr(d_x), _ptr(d_y), n, _ptr(d_grad), _ptr(ws),
+                                _nbytes(ws), _stream(stream)))
+
+
+def mlp_splitters(d_w, d_knots, log2B: int, d_t, stream=None):
+    _check(lib().elsar_mlp_splitters(_ptr(d_w), _ptr(d_knots), log2B, _ptr(d_t), _stream(stream)))
 
 
 # ---- device model buffer layout (read back for inspection and parity tests)
@@ -205,5 +226,15 @@ def read_model(d_model, p: Params, n: int):
     off = int(hdr["nodes_off"])
     nodes = np.frombuffer(buf[off:off + nn * NODE_BYTES].tobytes(), dtype=ndt)
     so = int(hdr["splitters_off"])
-    spl = np.frombuffer(buf[so:so + 8 * (1 << int(hdr["log2B"]))].tobytes(), dtype=np.uint64)
-    return {k: hdr[k].item() for k in hdr.dtype.names}, nodes, spl
+    B = 1 << int(hdr["log2B"])
+    spl = np.frombuffer(buf[so:so + 8 * B].tobytes(), dtype=np.uint64)
+    h = {k: hdr[k].item() for k in hdr.dtype.names}
+    # after the splitters: the radix index, then the network's knots and weights
+    up = lambda v: (v + 255) & ~255
+    lut_off = so + up(8 * B)
+    cells = ((95**9 - 1) >> 42) + 2
+    knots_off = lut_off + up(4 * cells)
+    w_off = knots_off + 256
+    h["mlp_knots"] = np.frombuffer(buf[knots_off:knots_off + 104].tobytes(), dtype=np.uint64).copy()
+    h["mlp_w"] = np.frombuffer(buf[w_off:w_off + 1505 * 4].tobytes(), dtype=np.float32).copy()
+    return h, nodes, spl

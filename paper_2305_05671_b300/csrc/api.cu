@@ -7,6 +7,7 @@
 
 #include "../../include/elsar.h"
 #include "common.cuh"
+#include "mlp.cuh"
 
 namespace elsar {
 size_t sort_smem_bytes(uint32_t cap);
@@ -89,8 +90,13 @@ elsar_status resolve(uint64_t n, const elsar_params* p, Resolved* r) {
 
 struct Layout {
   size_t ctrl, model, pairsA, pairsB, bin_off, part_off, cuts, cursor, items, item_flag, oversize, samp, pnode, sums,
-      fc, total;
+      fc, mlp_phi, mlp_y, mlp_partial, mlp_m, mlp_v, swap, judge, total;
 };
+
+constexpr uint64_t kMlpTrainMax = 2000000;  // keys the network trains on (every k-th of the sorted sample)
+constexpr uint32_t kMlpBatch = 65536, kMlpEpochs = 20, kMlpGrid = 512;
+
+uint64_t mlp_ntrain(uint64_t S) { return S < kMlpTrainMax ? S : kMlpTrainMax; }
 
 size_t up(size_t v) { return (v + 255) & ~(size_t)255; }
 
@@ -119,6 +125,15 @@ Layout layout(uint64_t n, const Resolved& r) {
   L.pnode = take(r.S * 4);
   L.sums = take(cap * 48);
   L.fc = take(cap * 8);  // split fanouts + child offsets of one level
+  const bool mlp = r.kind == ELSAR_MODEL_MLP;
+  const uint64_t nt = mlp ? mlp_ntrain(r.S) : 0;
+  L.mlp_phi = take(nt * 12 * 4);
+  L.mlp_y = take(nt * 4);
+  L.mlp_partial = take(mlp ? (size_t)kMlpGrid * kMlpParamCount * 4 : 0);
+  L.mlp_m = take(mlp ? kMlpParamCount * 4 : 0);
+  L.mlp_v = take(mlp ? kMlpParamCount * 4 : 0);
+  L.swap = take(mlp ? B * 8 : 0);
+  L.judge = take(mlp ? B * 8 : 0);
   L.total = o;
   return L;
 }
@@ -139,12 +154,28 @@ elsar_status common_checks(uint64_t n, const void* d_ws, size_t ws_bytes, const 
 
 const uint64_t* splitters_in(const void* d_model, const Resolved& r) {
   if (!d_model) return nullptr;
-  return reinterpret_cast<const uint64_t*>(static_cast<const uint8_t*>(d_model) + 256 +
-                                           node_cap_for(r.S, r.T) * sizeof(DNode));
+  return reinterpret_cast<const uint64_t*>(static_cast<const uint8_t*>(d_model) + model_layout(r.S, r.log2B, r.T).splitters);
+}
+
+const uint32_t* lut_in(const void* d_model, const Resolved& r) {
+  if (!d_model) return nullptr;
+  return reinterpret_cast<const uint32_t*>(static_cast<const uint8_t*>(d_model) + model_layout(r.S, r.log2B, r.T).lut);
+}
+
+struct FitResult {
+  uint32_t nodes = 0, kind = ELSAR_MODEL_RMI, fallback = 0;
+};
+
+// max / mean of a judge histogram (J buckets)
+double max_over_mean(const std::string& h, uint32_t J, uint64_t total) {
+  const uint32_t* c = reinterpret_cast<const uint32_t*>(h.data());
+  uint32_t mx = 0;
+  for (uint32_t j = 0; j < J; ++j) mx = c[j] > mx ? c[j] : mx;
+  return total ? (double)mx * J / (double)total : 0.0;
 }
 
 elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* d_model, void* d_ws, const Layout& L,
-                    cudaStream_t st, uint32_t* launches, uint32_t* nodes) {
+                    cudaStream_t st, uint32_t* launches, FitResult* res) {
   FitArgs f = {};
   f.records = static_cast<const uint8_t*>(d_records);
   f.n = n;
@@ -162,8 +193,88 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
   f.ctrl = at<uint32_t>(d_ws, L.ctrl);
   f.stream = st;
   f.launches = launches;
-  cudaError_t e = fit_rmi(f, nodes);
+  const uint64_t* sorted = nullptr;
+  cudaError_t e = fit_rmi(f, &res->nodes, &sorted);
   if (e != cudaSuccess) return cuda_fail(e, "fit");
+  res->kind = ELSAR_MODEL_RMI;
+  res->fallback = 0;
+  if (r.kind != ELSAR_MODEL_MLP) return ELSAR_OK;
+  // ---- the learned network: train, derive its splitters, let the RMI judge it
+  const ModelLayout ml = model_layout(r.S, r.log2B, r.T);
+  uint8_t* mb = static_cast<uint8_t*>(d_model);
+  uint64_t* T = reinterpret_cast<uint64_t*>(mb + ml.mlp_knots);
+  float* w = reinterpret_cast<float*>(mb + ml.mlp_w);
+  uint64_t* rmi_t = reinterpret_cast<uint64_t*>(mb + ml.splitters);
+  uint64_t* mlp_t = reinterpret_cast<uint64_t*>(mb + ml.alt_splitters);
+  MlpTrainArgs ta = {};
+  ta.sorted = sorted;
+  ta.S = r.S;
+  ta.ntrain = mlp_ntrain(r.S);
+  ta.batch = kMlpBatch;
+  ta.epochs = kMlpEpochs;
+  ta.lr = 1e-3f;
+  ta.T = T;
+  ta.w = w;
+  ta.m = at<float>(d_ws, L.mlp_m);
+  ta.v = at<float>(d_ws, L.mlp_v);
+  ta.phi = at<float>(d_ws, L.mlp_phi);
+  ta.y = at<float>(d_ws, L.mlp_y);
+  ta.partial = at<float>(d_ws, L.mlp_partial);
+  ta.grid = kMlpGrid;
+  ta.stream = st;
+  ta.launches = launches;
+  if ((e = mlp_train(ta)) != cudaSuccess) return cuda_fail(e, "mlp train");
+  if ((e = mlp_splitters(w, T, r.log2B, mlp_t, st)) != cudaSuccess) return cuda_fail(e, "mlp splitters");
+  // held-out keys (seed + 1) classified by both splitter sets into J judge buckets
+  uint64_t* held = sorted == f.samp ? f.samp + r.S : f.samp;
+  uint32_t log2J = 1;
+  while (log2J < r.log2B && (64ull << (log2J + 1)) <= r.S) ++log2J;
+  const uint32_t J = 1u << log2J;
+  uint32_t* hj = at<uint32_t>(d_ws, L.judge);
+  if ((e = sample_keys(f.records, n, r.S, r.seed + 1, held, st)) != cudaSuccess) return cuda_fail(e, "held-out");
+  if ((e = judge_histogram(held, r.S, rmi_t, r.log2B, log2J, hj, st)) != cudaSuccess) return cuda_fail(e, "judge");
+  if ((e = judge_histogram(held, r.S, mlp_t, r.log2B, log2J, hj + J, st)) != cudaSuccess) return cuda_fail(e, "judge");
+  // boundary check: F at the smallest and largest sample keys
+  float* Fb = reinterpret_cast<float*>(hj + 2 * J);
+  if ((e = mlp_eval(w, T, T, 13, Fb, st)) != cudaSuccess) return cuda_fail(e, "mlp eval");
+  std::string hh((size_t)2 * J * 4 + 13 * 4, '\0');
+  e = cudaMemcpyAsync(&hh[0], hj, hh.size(), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "judge readback");
+  const double rmi_mm = max_over_mean(hh.substr(0, (size_t)J * 4), J, r.S);
+  const double mlp_mm = max_over_mean(hh.substr((size_t)J * 4, (size_t)J * 4), J, r.S);
+  const float* Fk = reinterpret_cast<const float*>(hh.data() + (size_t)2 * J * 4);
+  // coarse sanity of the ends (the held-out balance below judges the rest)
+  const bool boundary_ok = Fk[0] < 1.0f / 16 && Fk[12] > 1.0f - 1.0f / 16;
+  if (!boundary_ok) res->fallback = 1;
+  else if (mlp_mm > rmi_mm) res->fallback = 2;
+  if (res->fallback == 0) {
+    // the network wins: its splitters become the active ones, the RMI's are kept as the alternate
+    uint64_t* tmp = at<uint64_t>(d_ws, L.swap);
+    const size_t bytes = (size_t)8 << r.log2B;
+    cudaMemcpyAsync(tmp, rmi_t, bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(rmi_t, mlp_t, bytes, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(mlp_t, tmp, bytes, cudaMemcpyDeviceToDevice, st);
+    if ((e = build_fine_lut(rmi_t, r.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut), st)) != cudaSuccess)
+      return cuda_fail(e, "lut");
+    res->kind = ELSAR_MODEL_MLP;
+  }
+  if ((e = set_model_kind(d_model, res->kind, res->fallback, st)) != cudaSuccess) return cuda_fail(e, "header");
+  *launches += 6;
+  return ELSAR_OK;
+}
+
+// The network's partitions failed the full-data check: restore the RMI's splitters.
+elsar_status revert_to_rmi(void* d_model, const Resolved& r, void* d_ws, const Layout& L, cudaStream_t st,
+                           uint32_t fallback) {
+  const ModelLayout ml = model_layout(r.S, r.log2B, r.T);
+  uint8_t* mb = static_cast<uint8_t*>(d_model);
+  const size_t bytes = (size_t)8 << r.log2B;
+  cudaError_t e = cudaMemcpyAsync(mb + ml.splitters, mb + ml.alt_splitters, bytes, cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess) e = build_fine_lut(reinterpret_cast<uint64_t*>(mb + ml.splitters), r.log2B,
+                                           reinterpret_cast<uint32_t*>(mb + ml.lut), st);
+  if (e == cudaSuccess) e = set_model_kind(d_model, ELSAR_MODEL_RMI, fallback, st);
+  if (e != cudaSuccess) return cuda_fail(e, "revert");
   return ELSAR_OK;
 }
 
@@ -174,7 +285,7 @@ PartArgs part_args(const void* d_model, const void* d_records, uint64_t n, const
   a.records = static_cast<const uint8_t*>(d_records);
   a.n = n;
   a.splitters = splitters_in(d_model, r);
-  a.lut = d_model ? reinterpret_cast<const uint32_t*>(a.splitters + (1ull << r.log2B)) : nullptr;
+  a.lut = lut_in(d_model, r);
   a.log2B = r.log2B;
   a.P = r.P;
   a.balance = r.balance;
@@ -281,9 +392,9 @@ elsar_status elsar_fit_model(const void* d_records, uint64_t n, const elsar_para
   if (!d_records || !aligned(d_records, 4)) return fail(ELSAR_EINVAL, "records must be non-null and 4-byte aligned");
   if (!d_model || !aligned(d_model, 256)) return fail(ELSAR_EINVAL, "model buffer must be 256-byte aligned");
   if (model_bytes < model_bytes_for(r.S, r.log2B, r.T)) return fail(ELSAR_ENOMEM, "model buffer too small");
-  if (r.kind != ELSAR_MODEL_RMI) return fail(ELSAR_EUNSUPPORTED, "model_kind MLP is not available in this build");
-  uint32_t launches = 0, nodes = 0;
-  return do_fit(d_records, n, r, d_model, d_ws, L, (cudaStream_t)stream, &launches, &nodes);
+  uint32_t launches = 0;
+  FitResult fr;
+  return do_fit(d_records, n, r, d_model, d_ws, L, (cudaStream_t)stream, &launches, &fr);
 }
 
 elsar_status elsar_partition(const void* d_model, const void* d_records, uint64_t n, const elsar_params* p,
@@ -346,15 +457,15 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
   const uint8_t* o8 = static_cast<const uint8_t*>(d_out);
   if (i8 < o8 + n * ELSAR_RECORD_BYTES && o8 < i8 + n * ELSAR_RECORD_BYTES)
     return fail(ELSAR_EINVAL, "input and output records overlap");
-  if (r.kind != ELSAR_MODEL_RMI) return fail(ELSAR_EUNSUPPORTED, "model_kind MLP is not available in this build");
   cudaStream_t st = (cudaStream_t)stream;
   cudaEvent_t ev[7] = {};
   if (stats)
     for (auto& e : ev) cudaEventCreate(&e);
   if (ev[0]) cudaEventRecord(ev[0], st);
-  uint32_t launches = 0, nodes = 0;
+  uint32_t launches = 0;
+  FitResult fr;
   void* model = at<void>(d_ws, L.model);
-  s = do_fit(d_in, n, r, model, d_ws, L, st, &launches, &nodes);
+  s = do_fit(d_in, n, r, model, d_ws, L, st, &launches, &fr);
   if (s == ELSAR_OK) {
     if (ev[1]) cudaEventRecord(ev[1], st);
     PartArgs a = part_args(model, d_in, n, r, at<void>(d_ws, L.pairsB), at<uint32_t>(d_ws, L.bin_off),
@@ -364,6 +475,22 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
     a.ev[2] = ev[4];
     cudaError_t e = partition_records(a);
     if (e != cudaSuccess) s = cuda_fail(e, "partition");
+    if (s == ELSAR_OK && fr.kind == ELSAR_MODEL_MLP) {
+      // full-data check of the network's partitions: above 1.1 x the mean, the RMI takes over
+      std::string po((r.P + 1) * 8, '\0');
+      e = cudaMemcpyAsync(&po[0], at<uint64_t>(d_ws, L.part_off), po.size(), cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) return cuda_fail(e, "partition readback");
+      const uint64_t* off = reinterpret_cast<const uint64_t*>(po.data());
+      uint64_t mx = 0;
+      for (uint32_t q = 0; q < r.P; ++q) mx = off[q + 1] - off[q] > mx ? off[q + 1] - off[q] : mx;
+      if ((double)mx * r.P > 1.1 * (double)n) {
+        fr.kind = ELSAR_MODEL_RMI;
+        fr.fallback = 3;
+        s = revert_to_rmi(model, r, d_ws, L, st, 3);
+        if (s == ELSAR_OK && (e = partition_records(a)) != cudaSuccess) s = cuda_fail(e, "partition");
+      }
+    }
   }
   if (s == ELSAR_OK)
     s = do_sort_partitions(d_in, n, r, at<void>(d_ws, L.pairsB), at<uint32_t>(d_ws, L.bin_off), d_out, d_ws, L, st,
@@ -386,7 +513,9 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
       stats->pass_ms[3] = ms(3, 4);
       stats->pass_ms[4] = ms(5, 6);
       stats->launches = launches;
-      stats->model_nodes = nodes;
+      stats->model_nodes = fr.nodes;
+      stats->model_used = fr.kind;
+      stats->fallback_reason = fr.fallback;
       uint32_t c[4];
       cudaMemcpy(c, at<uint32_t>(d_ws, L.ctrl), sizeof c, cudaMemcpyDeviceToHost);
       stats->num_items = c[kNumItems];
@@ -422,6 +551,42 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
     return cuda_fail(e, "copy out");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
   return ELSAR_OK;
+}
+
+size_t elsar_mlp_grad_workspace(uint64_t n) {
+  return ((n * 12 * 4 + 255) & ~(size_t)255) + (size_t)kMlpGrid * kMlpParamCount * 4;
+}
+
+elsar_status elsar_mlp_eval(const float* d_w, const uint64_t* d_knots, const uint64_t* d_x, uint64_t n, float* d_F,
+                            elsar_stream_t stream) {
+  g_err.clear();
+  if (n >= (1ull << 32)) return fail(ELSAR_EUNSUPPORTED, "n must be < 2^32");
+  if (!d_w || !d_knots || (n && (!d_x || !d_F))) return fail(ELSAR_EINVAL, "null buffer");
+  if (!n) return ELSAR_OK;
+  cudaError_t e = mlp_eval(d_w, d_knots, d_x, n, d_F, (cudaStream_t)stream);
+  return e == cudaSuccess ? ELSAR_OK : cuda_fail(e, "mlp eval");
+}
+
+elsar_status elsar_mlp_grad(const float* d_w, const uint64_t* d_knots, const uint64_t* d_x, const float* d_y,
+                            uint64_t n, float* d_grad, void* d_ws, size_t ws_bytes, elsar_stream_t stream) {
+  g_err.clear();
+  if (n == 0 || n >= (1ull << 32)) return fail(ELSAR_EINVAL, "n must be in [1, 2^32)");
+  if (!d_w || !d_knots || !d_x || !d_y || !d_grad || !d_ws || !aligned(d_ws, 256))
+    return fail(ELSAR_EINVAL, "null or misaligned buffer");
+  if (ws_bytes < elsar_mlp_grad_workspace(n)) return fail(ELSAR_ENOMEM, "workspace too small");
+  float* phi = static_cast<float*>(d_ws);
+  float* partial = at<float>(d_ws, (n * 12 * 4 + 255) & ~(size_t)255);
+  cudaError_t e = mlp_grad(d_w, d_knots, d_x, d_y, n, phi, partial, kMlpGrid, d_grad, (cudaStream_t)stream);
+  return e == cudaSuccess ? ELSAR_OK : cuda_fail(e, "mlp grad");
+}
+
+elsar_status elsar_mlp_splitters(const float* d_w, const uint64_t* d_knots, uint32_t log2B, uint64_t* d_t,
+                                 elsar_stream_t stream) {
+  g_err.clear();
+  if (!d_w || !d_knots || !d_t) return fail(ELSAR_EINVAL, "null buffer");
+  if (log2B < 1 || log2B > 22) return fail(ELSAR_EINVAL, "log2B must be in [1, 22]");
+  cudaError_t e = mlp_splitters(d_w, d_knots, log2B, d_t, (cudaStream_t)stream);
+  return e == cudaSuccess ? ELSAR_OK : cuda_fail(e, "mlp splitters");
 }
 
 const char* elsar_status_str(elsar_status s) {

@@ -164,9 +164,20 @@ struct FitArgs {
   uint32_t* launches;
 };
 
-size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T);
 uint64_t node_cap_for(uint64_t S, uint32_t T);
-cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out);
+
+// Byte offsets inside the device model buffer.
+struct ModelLayout {
+  size_t nodes, splitters, lut, mlp_knots, mlp_w, alt_splitters, bytes;
+};
+ModelLayout model_layout(uint64_t S, uint32_t log2B, uint32_t T);
+inline size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T) { return model_layout(S, log2B, T).bytes; }
+
+// fits the RMI; *sorted_out = the buffer holding the sorted sample (a.samp or a.samp + S)
+cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sorted_out);
+cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, uint64_t* out, cudaStream_t st);
+cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* lut, cudaStream_t st);
+cudaError_t set_model_kind(void* model, uint32_t kind, uint32_t fallback, cudaStream_t st);
 
 struct PartArgs {
   const uint8_t* records;

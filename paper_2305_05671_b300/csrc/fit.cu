@@ -461,8 +461,46 @@ __global__ void write_header(ModelHeader h, ModelHeader* dst, const uint32_t* ct
 
 uint64_t node_cap_for(uint64_t S, uint32_t T) { return 4 * ((S + T - 1) / T) + 1024; }
 
-size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T) {
-  return 256 + node_cap_for(S, T) * sizeof(DNode) + ((size_t)8 << log2B) + (size_t)kFineLutCells * 4;
+ModelLayout model_layout(uint64_t S, uint32_t log2B, uint32_t T) {
+  auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
+  ModelLayout L;
+  size_t o = 256;
+  L.nodes = o;
+  o += up(node_cap_for(S, T) * sizeof(DNode));
+  L.splitters = o;
+  o += up((size_t)8 << log2B);
+  L.lut = o;
+  o += up((size_t)kFineLutCells * 4);
+  L.mlp_knots = o;
+  o += 256;
+  L.mlp_w = o;
+  o += up(1505 * 4);
+  L.alt_splitters = o;
+  o += up((size_t)8 << log2B);
+  L.bytes = o;
+  return L;
+}
+
+__global__ void write_kind_kernel(ModelHeader* h, uint32_t kind, uint32_t fallback) {
+  h->kind = kind;
+  h->fallback = fallback;
+}
+
+cudaError_t set_model_kind(void* model, uint32_t kind, uint32_t fallback, cudaStream_t st) {
+  write_kind_kernel<<<1, 1, 0, st>>>(reinterpret_cast<ModelHeader*>(model), kind, fallback);
+  return cudaGetLastError();
+}
+
+cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, uint64_t* out, cudaStream_t st) {
+  const unsigned grid = (unsigned)umin64((S + 255) / 256, (uint64_t)sm_count() * 8);
+  sample_kernel<<<grid ? grid : 1, 256, 0, st>>>(records, n, S, seed, out);
+  return cudaGetLastError();
+}
+
+cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* lut, cudaStream_t st) {
+  const uint32_t B = 1u << log2B;
+  fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, log2B, lut);
+  return cudaGetLastError();
 }
 
 int sm_count() {
@@ -476,7 +514,7 @@ int sm_count() {
   return cached;
 }
 
-cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out) {
+cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sorted_out) {
   const uint64_t S = a.S;
   const uint64_t cap = node_cap_for(S, a.T);
   uint8_t* mb = static_cast<uint8_t*>(a.model);
@@ -486,9 +524,10 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out) {
   h.log2B = a.log2B;
   h.S = S;
   h.node_cap = cap;
-  h.nodes_off = 256;
-  h.splitters_off = 256 + cap * sizeof(DNode);
-  h.bytes = model_bytes_for(S, a.log2B, a.T);
+  const ModelLayout ml = model_layout(S, a.log2B, a.T);
+  h.nodes_off = ml.nodes;
+  h.splitters_off = ml.splitters;
+  h.bytes = ml.bytes;
   h.T = a.T;
   h.Dmax = a.Dmax;
   DNode* nodes = reinterpret_cast<DNode*>(mb + h.nodes_off);
@@ -513,6 +552,7 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out) {
     dst = tmp;
   }
   const uint64_t* x = src;
+  if (sorted_out) *sorted_out = src;
   // 3. RMI, breadth first, one level per round
   cudaMemsetAsync(a.sums, 0, 6 * sizeof(uint64_t), st);
   const unsigned pgrid = (unsigned)umin64((S + 255) / 256, (uint64_t)sms * 8);
@@ -543,8 +583,7 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out) {
   // 4. splitters of the fine bins
   const uint32_t B = 1u << a.log2B;
   splitter_kernel<<<(B + 127) / 128, 128, 0, st>>>(nodes, a.log2B, splitters);
-  fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, a.log2B,
-                                                   reinterpret_cast<uint32_t*>(splitters + B));
+  fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut));
   write_header<<<1, 1, 0, st>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
   L += 3;
   *nodes_out = host_ctrl[3];

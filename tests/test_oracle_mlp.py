@@ -1,0 +1,139 @@
+"""Pins for the oracle's monotone MLP CDF model (the learned model the GPU trains).
+
+The network is not in the paper (whose Sec. 3.1 model is an RMI), so these pins
+come from mathematics: closed forms of hand-set networks, the chain rule
+checked against central finite differences, FP32 vs FP64 agreement,
+monotonicity, and a trained network beating a single least-squares line.
+"""
+import numpy as np
+import pytest
+
+S = oracle_slices = None
+
+
+def _w(rng, scale=1.0):
+    w = rng.random(1505) * scale
+    w[384:416] = rng.normal(0, 1, 32)  # b1
+    w[1440:1472] = rng.normal(0, 1, 32)  # b2
+    w[1472:1504] *= 2.0 / 32  # w3
+    w[1504] = 0.0
+    w[0:384] *= 2.0 / 12
+    w[416:1440] *= 2.0 / 32
+    return w
+
+
+def test_closed_form_forward(orc):
+    w = np.zeros(1505)
+    w[1472:1504] = 0.02
+    w[1504] = 0.3
+    phi = np.random.default_rng(0).random((5, 12))
+    # every hidden unit sees 0 -> sigma(0) = 1/2; z = b3 + 32 * 0.02 * 1/2
+    assert np.allclose(orc.mlp_forward64(w, phi), 0.3 + 0.32)
+    assert np.allclose(orc.mlp_forward32(w.astype(np.float32), phi.astype(np.float32)), 0.62, atol=1e-7)
+    # sigma(1) = 3/4 for one path: W1[0,0] = 1, phi_0 = 1 -> h1_0 = 3/4; W2[0,0] = 4 -> p2_0 = 3 -> h2_0 = 7/8
+    w = np.zeros(1505)
+    w[0] = 1.0
+    w[416] = 4.0
+    w[1472] = 1.0
+    phi = np.zeros((1, 12))
+    phi[0, 0] = 1.0
+    assert orc.mlp_forward64(w, phi)[0] == pytest.approx(7 / 8)
+    # output clamps to [0, 1]
+    w[1504] = 5.0
+    assert orc.mlp_forward64(w, phi)[0] == 1.0
+    w[1504] = -5.0
+    assert orc.mlp_forward64(w, phi)[0] == 0.0
+
+
+def test_features_are_ramps_between_knots(orc):
+    x = np.sort(np.random.default_rng(1).integers(0, 95**9, 100001, dtype=np.uint64))
+    T = orc.mlp_knots(x)
+    assert T[0] == x[0] and T[12] == x[-1] and np.all(np.diff(T.astype(np.float64)) >= 0)
+    phi = orc.mlp_features(T, T)
+    for m in range(12):
+        assert phi[m, m] == 0.0 and phi[m + 1, m] == 1.0  # 0 at its knot, 1 at the next
+        assert np.all(phi[: m + 1, m] == 0.0) and np.all(phi[m + 1:, m] == 1.0)
+    mid = T[:12] + (T[1:] - T[:12]) // np.uint64(2)
+    pm = orc.mlp_features(T, mid)
+    assert np.allclose(np.diag(pm), 0.5, atol=1e-6)
+    # monotone in the key
+    f = orc.mlp_features(T, x)
+    assert np.all(np.diff(f, axis=0) >= 0)
+
+
+def test_backward_matches_central_differences(orc):
+    rng = np.random.default_rng(2)
+    w = _w(rng)
+    phi = rng.random((64, 12))
+    y = rng.random(64)
+    F = orc.mlp_forward64(w, phi)
+    assert np.all((F > 0) & (F < 1))  # away from the clamp's kinks
+    g = orc.mlp_grad64(w, phi, y)
+    idx = np.concatenate([rng.choice(1505, 60, replace=False), [0, 383, 384, 416, 1439, 1440, 1472, 1504]])
+
+    def loss(v):
+        return np.mean((orc.mlp_forward64(v, phi) - y) ** 2)
+
+    for i in idx:
+        h = 1e-6 * max(1.0, abs(w[i]))
+        wp, wm = w.copy(), w.copy()
+        wp[i] += h
+        wm[i] -= h
+        fd = (loss(wp) - loss(wm)) / (2 * h)
+        assert g[i] == pytest.approx(fd, rel=1e-5, abs=1e-10), i
+
+
+def test_fp32_forward_within_1e5_of_fp64(orc):
+    rng = np.random.default_rng(3)
+    for _ in range(5):
+        w = _w(rng)
+        phi = rng.random((2000, 12)).astype(np.float32)
+        f32 = orc.mlp_forward32(w.astype(np.float32), phi)
+        f64 = orc.mlp_forward64(w.astype(np.float32).astype(np.float64), phi.astype(np.float64))
+        assert np.abs(f32 - f64).max() < 1e-5
+
+
+def test_nonnegative_weights_make_it_monotone(orc):
+    rng = np.random.default_rng(4)
+    x = np.sort(rng.integers(0, 95**9, 20001, dtype=np.uint64))
+    T = orc.mlp_knots(x)
+    probe = np.sort(rng.integers(0, 95**9, 50000, dtype=np.uint64))
+    phi = orc.mlp_features(T, probe).astype(np.float64)
+    for _ in range(3):
+        F = orc.mlp_forward64(_w(rng), phi)
+        assert np.all(np.diff(F) >= -1e-12)
+
+
+def test_training_beats_a_least_squares_line(orc, gen):
+    n = 200_000
+    recs = gen.generate_cpu(n, gen.KeySpec("zipf", s=1.3, dup=0.1, seed=5))
+    x = np.sort(orc.sample(recs, 20000, 1))
+    y = np.arange(x.size) / x.size
+    T = orc.mlp_knots(x)
+    phi = orc.mlp_features(T, x).astype(np.float64)
+    w0 = orc.mlp_init().astype(np.float64)
+    init_mse = np.mean((orc.mlp_forward64(w0, phi) - y) ** 2)
+    w, loss = orc.mlp_train64(w0, phi, y, batch=4096, epochs=20, lr=1e-3)
+    assert loss < init_mse
+    slope, icpt = np.polyfit(x.astype(np.float64), y, 1)
+    line_mse = np.mean((np.clip(slope * x.astype(np.float64) + icpt, 0, 1) - y) ** 2)
+    assert loss < line_mse / 10
+    # projection keeps every weight >= 0
+    for k in ("W1", "W2", "w3"):
+        a, b = orc.MLP_SLICES[k]
+        assert np.all(w[a:b] >= 0)
+
+
+def test_splitters_reproduce_the_fp32_bins(orc):
+    rng = np.random.default_rng(5)
+    x = np.sort(rng.integers(0, 95**9, 20001, dtype=np.uint64))
+    T = orc.mlp_knots(x)
+    w = _w(rng).astype(np.float32)
+    log2B = 8
+    t = orc.mlp_splitters(w, T, log2B)
+    assert t[0] == 0 and np.all(np.diff(t.astype(np.float64)) >= 0)
+    probe = np.sort(rng.integers(0, 95**9, 30000, dtype=np.uint64))
+    q = orc.bins_by_splitters(t, log2B, probe)
+    direct = np.minimum(255, np.floor(orc.mlp_forward32(w, orc.mlp_features(T, probe)) * 256)).astype(np.uint32)
+    assert np.mean(q == direct) > 0.999
+    assert np.all(np.diff(q.astype(np.int64)) >= 0)
