@@ -168,6 +168,50 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
                              void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
 
 /*
+ * Many independent record sets in one CUDA-graph-captured launch sequence
+ * (the batched form of the method; the paper sorts one file at a time and
+ * balances uneven partitions with dynamic thread scheduling, Sec. 7.3 -- here
+ * all sets' work items feed one persistent kernel).  Every set is sorted on
+ * its own, with its own model: a 1 % sample (seed + k for set k), its own RMI
+ * (Sec. 3.1) and its own fine bins; all sets share the passes.  Set k's
+ * sorted records go to d_out[k].
+ *
+ * elsar_batch_create builds a plan for fixed buffers and sizes: it uploads
+ * per-set tables into the workspace, and captures the whole sequence into a
+ * CUDA graph.  With tile_pairs == 0 it first autotunes -- the tile size, then
+ * the fine-bin density of each size class of sets (fewer than 2^15 records,
+ * fewer than 2^18, larger) -- by timing candidate graphs on the caller's
+ * data; the choice is cached per device and workload shape for the process
+ * (and in the file named by the environment variable ELSAR_TUNE_CACHE, if
+ * set).  Creation synchronises.  elsar_batch_run launches the graph on
+ * `stream` (asynchronous); elsar_batch_wait synchronises `stream` and reports
+ * a device-side timeout.  The plan keeps the buffer pointers: they must stay
+ * valid, and run/wait calls on one plan must not overlap.
+ * Limits: 1 <= num_sets <= 2^24, every n[k] > 0, the sum of n[k] < 2^32.
+ * Errors: EINVAL, ENOMEM (workspace below elsar_batch_workspace_size),
+ * EUNSUPPORTED, ECUDA.
+ */
+typedef struct elsar_batch elsar_batch;
+
+typedef struct elsar_batch_info {
+  uint32_t tile_pairs;              /* pairs per shared-memory tile chosen */
+  uint32_t records_per_bin_log2[3]; /* fine-bin density chosen per size class */
+  uint64_t total_records, total_bins, sample_keys;
+  uint32_t launches;    /* kernels in the captured sequence */
+  uint32_t tuning_runs; /* candidate graphs timed by the autotuner (0 if cached or fixed) */
+  float tuning_ms[16];  /* their times */
+} elsar_batch_info;
+
+size_t elsar_batch_workspace_size(const uint64_t* n, uint32_t num_sets, const elsar_params* p);
+elsar_status elsar_batch_create(const void* const* d_in, void* const* d_out, const uint64_t* n, uint32_t num_sets,
+                                const elsar_params* p, void* d_ws, size_t ws_bytes, elsar_stream_t stream,
+                                elsar_batch** out);
+elsar_status elsar_batch_run(elsar_batch* b, elsar_stream_t stream);
+elsar_status elsar_batch_wait(elsar_batch* b, elsar_stream_t stream);
+elsar_status elsar_batch_describe(const elsar_batch* b, elsar_batch_info* info);
+void elsar_batch_destroy(elsar_batch* b);
+
+/*
  * The learned CDF network (model_kind = ELSAR_MODEL_MLP) on its own, for
  * inspection and parity checks.  It is not in the paper, whose model
  * (Sec. 3.1) is the RMI; its definition: 12 features of a key encoding x are

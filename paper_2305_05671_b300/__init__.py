@@ -41,6 +41,12 @@ class _Stats(ctypes.Structure):
                 ("fallback_reason", ctypes.c_uint32)]
 
 
+class _BatchInfo(ctypes.Structure):
+    _fields_ = [("tile_pairs", ctypes.c_uint32), ("records_per_bin_log2", ctypes.c_uint32 * 3),
+                ("total_records", ctypes.c_uint64), ("total_bins", ctypes.c_uint64), ("sample_keys", ctypes.c_uint64),
+                ("launches", ctypes.c_uint32), ("tuning_runs", ctypes.c_uint32), ("tuning_ms", ctypes.c_float * 16)]
+
+
 @dataclass
 class Params:
     """elsar_params; zero means "library default"."""
@@ -86,6 +92,12 @@ def lib():
             "elsar_mlp_eval": (ctypes.c_int, [P, P, P, U64, P, P]),
             "elsar_mlp_grad": (ctypes.c_int, [P, P, P, P, U64, P, P, SZ, P]),
             "elsar_mlp_splitters": (ctypes.c_int, [P, P, ctypes.c_uint32, P, P]),
+            "elsar_batch_workspace_size": (SZ, [P, ctypes.c_uint32, PP]),
+            "elsar_batch_create": (ctypes.c_int, [P, P, P, ctypes.c_uint32, PP, P, SZ, P, ctypes.POINTER(P)]),
+            "elsar_batch_run": (ctypes.c_int, [P, P]),
+            "elsar_batch_wait": (ctypes.c_int, [P, P]),
+            "elsar_batch_describe": (ctypes.c_int, [P, ctypes.POINTER(_BatchInfo)]),
+            "elsar_batch_destroy": (None, [P]),
             "elsar_status_str": (ctypes.c_char_p, [ctypes.c_int]),
             "elsar_last_error": (ctypes.c_char_p, []),
         }
@@ -206,6 +218,52 @@ def mlp_splitters(d_w, d_knots, log2B: int, d_t, stream=None):
     _check(lib().elsar_mlp_splitters(_ptr(d_w), _ptr(d_knots), log2B, _ptr(d_t), _stream(stream)))
 
 
+class Batch:
+    """A plan sorting many record sets with one CUDA-graph launch (elsar_batch_*)."""
+
+    def __init__(self, d_ins, d_outs, p: Params | None = None, ws=None, stream=None):
+        import numpy as np
+        import torch
+
+        self.p = p or Params()
+        self.n = np.array([t.numel() // RECORD for t in d_ins], dtype=np.uint64)
+        K = len(d_ins)
+        self._ins = (ctypes.c_void_p * K)(*[t.data_ptr() for t in d_ins])
+        self._outs = (ctypes.c_void_p * K)(*[t.data_ptr() for t in d_outs])
+        self._keep = (d_ins, d_outs)
+        need = lib().elsar_batch_workspace_size(self.n.ctypes.data, K, ctypes.byref(self.p.c()))
+        self.ws = ws if ws is not None else torch.empty(max(256, need), dtype=torch.uint8, device=d_ins[0].device)
+        h = ctypes.c_void_p()
+        _check(lib().elsar_batch_create(self._ins, self._outs, self.n.ctypes.data, K, ctypes.byref(self.p.c()),
+                                        _ptr(self.ws), _nbytes(self.ws), _stream(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def run(self, stream=None):
+        _check(lib().elsar_batch_run(self.handle, _stream(stream)))
+
+    def wait(self, stream=None):
+        _check(lib().elsar_batch_wait(self.handle, _stream(stream)))
+
+    def info(self) -> dict:
+        i = _BatchInfo()
+        _check(lib().elsar_batch_describe(self.handle, ctypes.byref(i)))
+        return dict(tile_pairs=i.tile_pairs, records_per_bin_log2=list(i.records_per_bin_log2),
+                    total_records=i.total_records, total_bins=i.total_bins, sample_keys=i.sample_keys,
+                    launches=i.launches, tuning_runs=i.tuning_runs,
+                    tuning_ms=list(i.tuning_ms)[: min(16, i.tuning_runs)])
+
+    def close(self):
+        if self.handle:
+            lib().elsar_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 # ---- device model buffer layout (read back for inspection and parity tests)
 MODEL_HEADER_BYTES = 256
 NODE_BYTES = 64
@@ -221,7 +279,7 @@ def read_model(d_model, p: Params, n: int):
         ("nodes_off", "<u8"), ("splitters_off", "<u8"), ("bytes", "<u8"), ("T", "<u4"), ("Dmax", "<u4"),
         ("levels", "<u4"), ("fallback", "<u4")]))[0]
     ndt = np.dtype([("s", "<u4"), ("e", "<u4"), ("base", "<u8"), ("child0", "<u4"), ("fanout", "<u4"),
-                    ("shift", "<u4"), ("depth", "<u4"), ("a", "<f8"), ("b", "<f8"), ("c", "<f8"), ("h", "<f8")])
+                    ("shift", "<u4"), ("depth_set", "<u4"), ("a", "<f8"), ("b", "<f8"), ("c", "<f8"), ("h", "<f8")])
     nn = int(hdr["num_nodes"])
     off = int(hdr["nodes_off"])
     nodes = np.frombuffer(buf[off:off + nn * NODE_BYTES].tobytes(), dtype=ndt)

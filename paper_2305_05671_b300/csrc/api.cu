@@ -90,7 +90,7 @@ elsar_status resolve(uint64_t n, const elsar_params* p, Resolved* r) {
 
 struct Layout {
   size_t ctrl, model, pairsA, pairsB, bin_off, part_off, cuts, cursor, items, item_flag, oversize, samp, pnode, sums,
-      fc, mlp_phi, mlp_y, mlp_partial, mlp_m, mlp_v, swap, judge, total;
+      fc, sets, mlp_phi, mlp_y, mlp_partial, mlp_m, mlp_v, swap, judge, total;
 };
 
 constexpr uint64_t kMlpTrainMax = 2000000;  // keys the network trains on (every k-th of the sorted sample)
@@ -125,6 +125,7 @@ Layout layout(uint64_t n, const Resolved& r) {
   L.pnode = take(r.S * 4);
   L.sums = take(cap * 48);
   L.fc = take(cap * 8);  // split fanouts + child offsets of one level
+  L.sets = take(sizeof(SetInfo));
   const bool mlp = r.kind == ELSAR_MODEL_MLP;
   const uint64_t nt = mlp ? mlp_ntrain(r.S) : 0;
   L.mlp_phi = take(nt * 12 * 4);
@@ -191,6 +192,7 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
   f.sums = at<uint64_t>(d_ws, L.sums);
   f.fc = at<uint32_t>(d_ws, L.fc);
   f.ctrl = at<uint32_t>(d_ws, L.ctrl);
+  f.sets = at<SetInfo>(d_ws, L.sets);
   f.stream = st;
   f.launches = launches;
   const uint64_t* sorted = nullptr;

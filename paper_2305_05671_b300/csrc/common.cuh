@@ -27,12 +27,19 @@ __device__ __forceinline__ bool pair_less(const Pair& a, const Pair& b) {
 
 // One RMI node (64 bytes).  Internal: a = gamma, b = delta, c = scale.
 // Leaf: a = g, b = d, c = lo, h = hi (output constants of Sec. 3.1's model).
+// depth_set = depth (low 8 bits) | record set << 8 (batched fits hold one
+// tree per set; s, e are positions in the concatenated sorted samples).
 struct __align__(64) DNode {
-  uint32_t s, e;  // sample ranks covered
+  uint32_t s, e;  // sample positions covered
   uint64_t base;
   uint32_t child0, fanout;  // fanout 0 = leaf
-  uint32_t shift, depth;
+  uint32_t shift, depth_set;
   double a, b, c, h;
+};
+
+// Sample segment of one record set: sorted sample positions [soff, soff + S).
+struct SetInfo {
+  uint64_t soff, S;
 };
 
 struct ModelHeader {
@@ -41,6 +48,15 @@ struct ModelHeader {
   uint64_t nodes_off, splitters_off, bytes;
   uint32_t T, Dmax, levels, fallback;
 };
+
+// The k-th output of the SplitMix64 generator seeded with `seed` (Steele,
+// Lea, Flood 2014): the sample positions are mulhi64(SplitMix64_k(seed), n).
+__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
+  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
 
 // Key encoding (Sec. 4): 9 base-95 digits (ASCII - 32) of printable bytes.
 // w0 = bytes 0-3, w1 = bytes 4-7 as big-endian words; b8 = byte 8.  A byte
@@ -160,9 +176,34 @@ struct FitArgs {
   uint64_t* sums;   // node_cap * 6
   uint32_t* fc;     // 2 * node_cap: split fanouts, child offsets
   uint32_t* ctrl;   // 64 words
+  SetInfo* sets;    // one entry (single record set)
   cudaStream_t stream;
   uint32_t* launches;
 };
+
+// Level-by-level RMI construction over K trees at once (K record sets whose
+// sorted samples are concatenated; sets[k] gives each segment).  `host_sync`
+// reads the level sizes back (single-set path); otherwise a fixed number of
+// levels is launched and empty levels exit at once (capturable in a graph).
+struct RmiLevelsArgs {
+  const uint64_t* x;  // concatenated sorted samples
+  uint64_t S_total;
+  const SetInfo* sets;
+  uint32_t K, T, Dmax;
+  uint64_t node_cap;
+  DNode* nodes;
+  uint32_t* pnode;
+  uint64_t* sums;
+  uint32_t* fc;
+  uint32_t* ctrl;
+  bool host_sync;
+  cudaStream_t stream;
+  uint32_t* launches;
+};
+cudaError_t build_rmi_levels(const RmiLevelsArgs& a, uint32_t* nodes_out, uint32_t* levels_out);
+// Splitters of every set: set k's B_k = 1 << log2B[k] splitters at t + tbase[k], tree k rooted at node k.
+cudaError_t splitters_batch(const DNode* nodes, uint32_t K, const uint32_t* log2B, const uint64_t* tbase,
+                            uint64_t total_bins, uint64_t* t, cudaStream_t st);
 
 uint64_t node_cap_for(uint64_t S, uint32_t T);
 
@@ -203,9 +244,37 @@ struct PartArgs {
 cudaError_t partition_records(const PartArgs& a);
 cudaError_t build_items(const PartArgs& a);
 
+// many record sets (batched path): all sets share one fine-bin space, set k
+// owning bins [tbase[k], tbase[k] + 2^log2B[k]) and pair slots [poff[k], poff[k+1])
+struct BatchPartArgs {
+  const uint8_t* const* ins;  // device array of K record buffers
+  const uint64_t* poff;       // K+1
+  uint32_t K, B, tile_pairs;  // B = total bins
+  const uint64_t* splitters;  // B
+  const uint64_t* tbase;      // K+1
+  const uint32_t* log2B;      // K
+  Pair* pairs_in_order;
+  Pair* pairs;
+  uint32_t* bin_off;  // B+1
+  uint32_t* cursor;   // B
+  uint32_t* items;    // B+1
+  uint32_t* item_flag;
+  uint32_t* oversize;
+  uint32_t* ctrl;
+  cudaStream_t stream;
+  uint32_t* launches;
+};
+cudaError_t partition_batch(const BatchPartArgs& a);
+
 struct SortArgs {
   const uint8_t* records;
   uint8_t* out;
+  // batched path: per-set record buffers; items map to sets through tbase/poff
+  const uint8_t* const* ins;
+  uint8_t* const* outs;
+  const uint64_t* tbase;
+  const uint64_t* poff;
+  uint32_t K;
   uint64_t n;
   uint32_t log2B, P, schedule, tile_pairs;
   Pair* pairs;  // bin-ordered
@@ -221,6 +290,7 @@ struct SortArgs {
 };
 
 cudaError_t sort_items(const SortArgs& a);
+cudaError_t prepare_sort_kernel(uint32_t cap);  // kernel attributes, before any stream capture
 int sm_count();
 
 // control word indices

@@ -16,13 +16,6 @@ typedef unsigned __int128 u128;
 typedef __int128 i128;
 
 // ------------------------------------------------------------------ helpers
-__device__ __forceinline__ uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
-  uint64_t z = seed + (k + 1) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
 // Correctly rounded (to nearest even) unsigned 128-bit -> double: keep the
 // top 64 bits with the discarded bits ORed into bit 0 (a sticky bit below
 // the rounding position), let the hardware round 64 -> 53 bits, then scale
@@ -53,25 +46,6 @@ __device__ __forceinline__ uint32_t route(const DNode& v, uint64_t x) {
   if (!(t > 0.0)) return 0;
   if (t >= __uint2double_rn(v.fanout)) return v.fanout - 1;
   return __double2uint_rz(t);
-}
-
-__device__ __forceinline__ double model_cdf(const DNode* __restrict__ nodes, uint64_t x) {
-  uint32_t i = 0;
-  DNode v = nodes[0];
-  while (v.fanout) {
-    i = v.child0 + route(v, x);
-    v = nodes[i];
-  }
-  double y = __fma_rn(v.a, __ull2double_rn(local_u(v, x)), v.b);
-  if (y < v.c) return v.c;
-  if (y > v.h) return v.h;
-  return y;
-}
-
-__device__ __forceinline__ uint32_t model_bin(const DNode* __restrict__ nodes, uint64_t x, uint32_t log2B) {
-  uint32_t B = 1u << log2B;
-  uint32_t q = __double2uint_rz(__dmul_rn(model_cdf(nodes, x), __uint2double_rn(B)));
-  return q < B ? q : B - 1;
 }
 
 __device__ __forceinline__ void atomic_add_u128(uint64_t* p, u128 v) {
@@ -179,19 +153,37 @@ __global__ void __launch_bounds__(kMergeThreads) merge_pass_u64(const uint64_t* 
 }
 
 // ------------------------------------------------------------------ RMI, level by level
-__global__ void init_root(DNode* nodes, uint32_t* pnode, uint64_t S, uint32_t* ctrl) {
-  uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-  if (k == 0) {
-    DNode r = {};
-    r.s = 0;
-    r.e = (uint32_t)S;
-    nodes[0] = r;
-    ctrl[kLevelNodes + 0] = 0;
-    ctrl[kLevelNodes + 1] = 1;
-    ctrl[kLevelNodes + 2] = 0;
-    ctrl[kLevelNodes + 3] = 1;
+// K trees at once: tree k (record set k) has its root at node k and covers the
+// sorted-sample segment sets[k].  A single record set is K = 1.
+
+__device__ __forceinline__ uint32_t set_of_point(const SetInfo* sets, uint32_t K, uint64_t j) {
+  uint32_t lo = 0, hi = K - 1;  // largest k with soff_k <= j
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (sets[mid].soff <= j) lo = mid;
+    else hi = mid - 1;
   }
-  for (; k < S; k += (uint64_t)gridDim.x * blockDim.x) pnode[k] = 0;
+  return lo;
+}
+
+__global__ void init_roots(DNode* nodes, uint32_t* pnode, const SetInfo* __restrict__ sets, uint32_t K,
+                           uint64_t S_total, uint32_t* ctrl) {
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = t0; k < K; k += stride) {
+    DNode r = {};
+    r.s = (uint32_t)sets[k].soff;
+    r.e = (uint32_t)(sets[k].soff + sets[k].S);
+    r.depth_set = (uint32_t)k << 8;
+    nodes[k] = r;
+  }
+  if (t0 == 0) {
+    ctrl[kLevelNodes + 0] = 0;
+    ctrl[kLevelNodes + 1] = K;
+    ctrl[kLevelNodes + 2] = 0;
+    ctrl[kLevelNodes + 3] = K;
+    ctrl[kLevelNodes + 4] = 0;
+  }
+  for (uint64_t j = t0; j < S_total; j += stride) pnode[j] = set_of_point(sets, K, j);
 }
 
 // per-node base and shift, read by every point of the node
@@ -206,7 +198,8 @@ __device__ __forceinline__ void node_frame(const uint64_t* x, uint32_t s, uint32
 // exact sums Su, Suu, Sur of each node of the level (u = local coordinate, r = local rank)
 __global__ void level_sums(const uint64_t* __restrict__ x, uint64_t S, const DNode* __restrict__ nodes,
                            const uint32_t* __restrict__ pnode, uint64_t* sums, const uint32_t* ctrl) {
-  const uint32_t lv0 = ctrl[kLevelNodes + 0];
+  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
+  if (lv0 >= lv1) return;
   for (uint64_t k0 = blockIdx.x * (uint64_t)blockDim.x; k0 < S; k0 += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t k = k0 + threadIdx.x;
     uint32_t v = k < S ? pnode[k] : kSettled;
@@ -244,8 +237,8 @@ __global__ void level_sums(const uint64_t* __restrict__ x, uint64_t S, const DNo
 }
 
 // least-squares fit of every node of the level and its split decision
-__global__ void level_fit(const uint64_t* __restrict__ x, uint64_t S, DNode* nodes, const uint64_t* sums,
-                          uint32_t* fc, uint32_t T, uint32_t Dmax, const uint32_t* ctrl) {
+__global__ void level_fit(const uint64_t* __restrict__ x, DNode* nodes, const uint64_t* sums, uint32_t* fc, uint32_t T,
+                          uint32_t Dmax, const uint32_t* ctrl) {
   const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
   for (uint32_t v = lv0 + blockIdx.x * blockDim.x + threadIdx.x; v < lv1; v += gridDim.x * blockDim.x) {
     DNode nd = nodes[v];
@@ -273,7 +266,7 @@ __global__ void level_fit(const uint64_t* __restrict__ x, uint64_t S, DNode* nod
     nd.a = gamma;
     nd.b = delta;
     nd.c = 0.0;
-    bool split = n > 2u * T && nd.depth < Dmax && x[nd.s] < x[nd.e - 1];
+    bool split = n > 2u * T && (nd.depth_set & 0xFFu) < Dmax && x[nd.s] < x[nd.e - 1];
     if (split) {
       uint32_t f = (n + T - 1) / T;
       nd.fanout = f;
@@ -340,12 +333,11 @@ __global__ void __launch_bounds__(kScanThreads) level_scan(const uint32_t* __res
 
 // Every node of the level: internal nodes get their children, the rest
 // become leaves with their output constants (Sec. 3.1 reading: F clamped to
-// the leaf's sample-rank range).
+// the leaf's sample-rank range, ranks counted within its record set).
 __global__ void level_finalize(DNode* nodes, const uint32_t* __restrict__ fc, const uint32_t* __restrict__ childoff,
-                               uint64_t S, const uint32_t* ctrl) {
+                               const SetInfo* __restrict__ sets, const uint32_t* ctrl) {
   const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
   const bool overflow = ctrl[kLevelNodes + 4] != 0;
-  const double dS = __ull2double_rn(S);
   for (uint32_t v = lv0 + blockIdx.x * blockDim.x + threadIdx.x; v < lv1; v += gridDim.x * blockDim.x) {
     const uint32_t i = v - lv0;
     DNode nd = nodes[v];
@@ -354,15 +346,18 @@ __global__ void level_finalize(DNode* nodes, const uint32_t* __restrict__ fc, co
       nd.child0 = lv1 + childoff[i];
       nd.c = __ddiv_rn(__uint2double_rn(nd.fanout), __uint2double_rn(nd.e - nd.s));
     } else {
+      const SetInfo si = sets[nd.depth_set >> 8];
+      const double dS = __ull2double_rn(si.S);
+      const uint32_t rs = nd.s - (uint32_t)si.soff, re = nd.e - (uint32_t)si.soff;
       nd.fanout = 0;
       nd.child0 = 0;
-      const double lo = __ddiv_rn(__uint2double_rn(nd.s), dS), hi = __ddiv_rn(__uint2double_rn(nd.e), dS);
+      const double lo = __ddiv_rn(__uint2double_rn(rs), dS), hi = __ddiv_rn(__uint2double_rn(re), dS);
       if (nd.e == nd.s) {
         nd.a = 0.0;
         nd.b = lo;
       } else {
         const double g = __ddiv_rn(nd.a, dS);
-        const double d = __ddiv_rn(__dadd_rn(__uint2double_rn(nd.s), nd.b), dS);
+        const double d = __ddiv_rn(__dadd_rn(__uint2double_rn(rs), nd.b), dS);
         nd.a = g;
         nd.b = d;
       }
@@ -373,14 +368,12 @@ __global__ void level_finalize(DNode* nodes, const uint32_t* __restrict__ fc, co
   }
 }
 
-// Records of the next level (depth + 1, ranges set by level_route) and their sums zeroed.
+// Records of the next level zeroed with their sums (level_route sets ranges,
+// depth and set).
 __global__ void level_init_next(DNode* nodes, uint64_t* sums, const uint32_t* ctrl) {
-  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1], next = ctrl[kLevelNodes + 2];
-  if (lv0 >= lv1) return;
-  const uint32_t depth = nodes[lv0].depth + 1;
+  const uint32_t lv1 = ctrl[kLevelNodes + 1], next = ctrl[kLevelNodes + 2];
   for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < next; w += gridDim.x * blockDim.x) {
     DNode c = {};
-    c.depth = depth;
     nodes[lv1 + w] = c;
     uint64_t* sm = sums + (uint64_t)w * 6;
     for (int t = 0; t < 6; ++t) sm[t] = 0;
@@ -391,6 +384,7 @@ __global__ void level_init_next(DNode* nodes, uint64_t* sums, const uint32_t* ct
 __global__ void level_route(const uint64_t* __restrict__ x, uint64_t S, DNode* nodes, uint32_t* pnode,
                             const uint32_t* ctrl) {
   const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
+  if (lv0 >= lv1) return;
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < S; k += (uint64_t)gridDim.x * blockDim.x) {
     uint32_t v = pnode[k];
     if (v == kSettled || v < lv0 || v >= lv1) continue;
@@ -399,16 +393,19 @@ __global__ void level_route(const uint64_t* __restrict__ x, uint64_t S, DNode* n
       pnode[k] = kSettled;
       continue;
     }
+    const uint32_t cds = nd.depth_set + 1;  // same set, one level deeper
     uint32_t c = route(nd, x[k]);
     pnode[k] = nd.child0 + c;
     int pc = (k == nd.s) ? -1 : (int)route(nd, x[k - 1]);
     for (int cc = pc + 1; cc <= (int)c; ++cc) {
       nodes[nd.child0 + cc].s = (uint32_t)k;
+      nodes[nd.child0 + cc].depth_set = cds;
       if (cc >= 1) nodes[nd.child0 + cc - 1].e = (uint32_t)k;
     }
     if (k == nd.e - 1) {
       for (uint32_t cc = c + 1; cc < nd.fanout; ++cc) {
         nodes[nd.child0 + cc].s = nd.e;
+        nodes[nd.child0 + cc].depth_set = cds;
         nodes[nd.child0 + cc - 1].e = nd.e;
       }
       nodes[nd.child0 + nd.fanout - 1].e = nd.e;
@@ -420,6 +417,23 @@ __global__ void level_advance(uint32_t* ctrl) {
   uint32_t lv1 = ctrl[kLevelNodes + 1];
   ctrl[kLevelNodes + 0] = lv1;
   ctrl[kLevelNodes + 1] = lv1 + ctrl[kLevelNodes + 2];
+  ctrl[kLevelNodes + 2] = 0;
+}
+
+__device__ __forceinline__ double tree_cdf(const DNode* __restrict__ nodes, uint32_t root, uint64_t x) {
+  DNode v = nodes[root];
+  while (v.fanout) v = nodes[v.child0 + route(v, x)];
+  double y = __fma_rn(v.a, __ull2double_rn(local_u(v, x)), v.b);
+  if (y < v.c) return v.c;
+  if (y > v.h) return v.h;
+  return y;
+}
+
+__device__ __forceinline__ uint32_t tree_bin(const DNode* __restrict__ nodes, uint32_t root, uint64_t x,
+                                             uint32_t log2B) {
+  const uint32_t B = 1u << log2B;
+  const uint32_t q = __double2uint_rz(__dmul_rn(tree_cdf(nodes, root, x), __uint2double_rn(B)));
+  return q < B ? q : B - 1;
 }
 
 // fine-bin splitters: t[q] = smallest encoding whose bin is >= q (t[0] = 0);
@@ -434,10 +448,36 @@ __global__ void splitter_kernel(const DNode* __restrict__ nodes, uint32_t log2B,
     uint64_t lo = 0, hi = kEncTop;
     while (lo < hi) {
       uint64_t mid = lo + ((hi - lo) >> 1);
-      if (model_bin(nodes, mid, log2B) >= q) hi = mid;
+      if (tree_bin(nodes, 0, mid, log2B) >= q) hi = mid;
       else lo = mid + 1;
     }
     t[q] = lo;
+  }
+}
+
+// the same for K trees: global bin g belongs to set k with tbase[k] <= g < tbase[k+1]
+__global__ void splitter_batch_kernel(const DNode* __restrict__ nodes, uint32_t K, const uint32_t* __restrict__ log2B,
+                                      const uint64_t* __restrict__ tbase, uint64_t total, uint64_t* t) {
+  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t lo = 0, hi = K - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (tbase[mid] <= g) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint32_t k = lo, lb = log2B[k];
+    const uint32_t q = (uint32_t)(g - tbase[k]);
+    if (q == 0) {
+      t[g] = 0;
+      continue;
+    }
+    uint64_t a = 0, b = kEncTop;
+    while (a < b) {
+      const uint64_t mid = a + ((b - a) >> 1);
+      if (tree_bin(nodes, k, mid, lb) >= q) b = mid;
+      else a = mid + 1;
+    }
+    t[g] = a;
   }
 }
 
@@ -450,6 +490,11 @@ __global__ void fine_lut_kernel(const uint64_t* __restrict__ t, uint32_t log2B, 
     const uint64_t c1 = q + 1 < B ? (t[q + 1] + cell - 1) >> kFineLutShift : (uint64_t)kFineLutCells;
     for (uint64_t c = c0; c < c1 && c < kFineLutCells; ++c) lut[c] = q;
   }
+}
+
+__global__ void set_single_kernel(SetInfo* sets, uint64_t S) {
+  sets[0].soff = 0;
+  sets[0].S = S;
 }
 
 __global__ void write_header(ModelHeader h, ModelHeader* dst, const uint32_t* ctrl) {
@@ -514,6 +559,46 @@ int sm_count() {
   return cached;
 }
 
+cudaError_t build_rmi_levels(const RmiLevelsArgs& a, uint32_t* nodes_out, uint32_t* levels_out) {
+  cudaStream_t st = a.stream;
+  const int sms = sm_count();
+  const unsigned pgrid = (unsigned)umin64((a.S_total + 255) / 256 + 1, (uint64_t)sms * 8);
+  const unsigned ngrid = (unsigned)sms * 8;
+  cudaMemsetAsync(a.sums, 0, (size_t)a.K * 6 * sizeof(uint64_t), st);
+  init_roots<<<pgrid, 256, 0, st>>>(a.nodes, a.pnode, a.sets, a.K, a.S_total, a.ctrl);
+  *a.launches += 1;
+  uint32_t host_ctrl[4] = {0, a.K, 0, a.K};
+  uint32_t levels = 0;
+  const uint32_t max_levels = a.Dmax + 1;
+  for (uint32_t lv = 0; lv < max_levels; ++lv) {
+    level_sums<<<pgrid, 256, 0, st>>>(a.x, a.S_total, a.nodes, a.pnode, a.sums, a.ctrl);
+    level_fit<<<ngrid, 256, 0, st>>>(a.x, a.nodes, a.sums, a.fc, a.T, a.Dmax, a.ctrl);
+    level_scan<<<1, kScanThreads, 0, st>>>(a.fc, a.fc + a.node_cap, a.node_cap, a.ctrl);
+    level_finalize<<<ngrid, 256, 0, st>>>(a.nodes, a.fc, a.fc + a.node_cap, a.sets, a.ctrl);
+    level_init_next<<<ngrid, 256, 0, st>>>(a.nodes, a.sums, a.ctrl);
+    level_route<<<pgrid, 256, 0, st>>>(a.x, a.S_total, a.nodes, a.pnode, a.ctrl);
+    level_advance<<<1, 1, 0, st>>>(a.ctrl);
+    *a.launches += 7;
+    ++levels;
+    if (a.host_sync) {
+      cudaError_t err = cudaMemcpyAsync(host_ctrl, a.ctrl + kLevelNodes, sizeof(host_ctrl), cudaMemcpyDeviceToHost, st);
+      if (err != cudaSuccess) return err;
+      if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
+      if (host_ctrl[0] == host_ctrl[1]) break;
+    }
+  }
+  *nodes_out = host_ctrl[3];
+  *levels_out = levels;
+  return cudaGetLastError();
+}
+
+cudaError_t splitters_batch(const DNode* nodes, uint32_t K, const uint32_t* log2B, const uint64_t* tbase,
+                            uint64_t total_bins, uint64_t* t, cudaStream_t st) {
+  const unsigned grid = (unsigned)umin64((total_bins + 127) / 128 + 1, (uint64_t)sm_count() * 16);
+  splitter_batch_kernel<<<grid, 128, 0, st>>>(nodes, K, log2B, tbase, total_bins, t);
+  return cudaGetLastError();
+}
+
 cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sorted_out) {
   const uint64_t S = a.S;
   const uint64_t cap = node_cap_for(S, a.T);
@@ -554,31 +639,27 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sort
   const uint64_t* x = src;
   if (sorted_out) *sorted_out = src;
   // 3. RMI, breadth first, one level per round
-  cudaMemsetAsync(a.sums, 0, 6 * sizeof(uint64_t), st);
-  const unsigned pgrid = (unsigned)umin64((S + 255) / 256, (uint64_t)sms * 8);
-  init_root<<<pgrid, 256, 0, st>>>(nodes, a.pnode, S, a.ctrl);
+  set_single_kernel<<<1, 1, 0, st>>>(a.sets, S);
   ++L;
-  uint32_t levels = 0;
-  uint32_t host_ctrl[4] = {0, 1, 0, 1};
-  for (;;) {
-    const uint32_t cnt = host_ctrl[1] - host_ctrl[0];
-    level_sums<<<pgrid, 256, 0, st>>>(x, S, nodes, a.pnode, a.sums, a.ctrl);
-    level_fit<<<(unsigned)umin64((cnt + 255) / 256, (uint64_t)sms * 8), 256, 0, st>>>(
-        x, S, nodes, a.sums, a.fc, a.T, a.Dmax, a.ctrl);
-    const unsigned ngrid = (unsigned)umin64((cnt + 255) / 256, (uint64_t)sms * 8);
-    level_scan<<<1, kScanThreads, 0, st>>>(a.fc, a.fc + cap, cap, a.ctrl);
-    level_finalize<<<ngrid, 256, 0, st>>>(nodes, a.fc, a.fc + cap, S, a.ctrl);
-    level_init_next<<<(unsigned)umin64((2 * cnt + 255) / 256 + 1, (uint64_t)sms * 8), 256, 0, st>>>(nodes, a.sums, a.ctrl);
-    level_route<<<pgrid, 256, 0, st>>>(x, S, nodes, a.pnode, a.ctrl);
-    level_advance<<<1, 1, 0, st>>>(a.ctrl);
-    L += 7;
-    ++levels;
-    cudaError_t err = cudaMemcpyAsync(host_ctrl, a.ctrl + kLevelNodes, sizeof(host_ctrl), cudaMemcpyDeviceToHost, st);
-    if (err != cudaSuccess) return err;
-    err = cudaStreamSynchronize(st);
-    if (err != cudaSuccess) return err;
-    if (host_ctrl[2] == 0 || host_ctrl[0] == host_ctrl[1]) break;
-  }
+  RmiLevelsArgs la = {};
+  la.x = x;
+  la.S_total = S;
+  la.sets = a.sets;
+  la.K = 1;
+  la.T = a.T;
+  la.Dmax = a.Dmax;
+  la.node_cap = cap;
+  la.nodes = nodes;
+  la.pnode = a.pnode;
+  la.sums = a.sums;
+  la.fc = a.fc;
+  la.ctrl = a.ctrl;
+  la.host_sync = true;
+  la.stream = st;
+  la.launches = a.launches;
+  uint32_t nodes_total = 0, levels = 0;
+  cudaError_t err = build_rmi_levels(la, &nodes_total, &levels);
+  if (err != cudaSuccess) return err;
   h.levels = levels;
   // 4. splitters of the fine bins
   const uint32_t B = 1u << a.log2B;
@@ -586,7 +667,7 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sort
   fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut));
   write_header<<<1, 1, 0, st>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
   L += 3;
-  *nodes_out = host_ctrl[3];
+  *nodes_out = nodes_total;
   return cudaGetLastError();
 }
 

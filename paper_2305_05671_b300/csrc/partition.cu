@@ -156,12 +156,11 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* e
 
 // Single CTA: bin offsets (exclusive scan of the histogram), scatter cursors,
 // max bin.  Coalesced tiles of kScanThreads bins with a running carry.
-__global__ void __launch_bounds__(kScanThreads) scan_bins(const uint32_t* hist, uint32_t log2B,
+__global__ void __launch_bounds__(kScanThreads) scan_bins(const uint32_t* hist, uint32_t B,
                                                           uint32_t* __restrict__ bin_off, uint32_t* cursor,
                                                           uint32_t* ctrl) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t carry_sh;
-  const uint32_t B = 1u << log2B;
   if (threadIdx.x == 0) carry_sh = 0;
   uint32_t mx = 0;
   __syncthreads();
@@ -235,12 +234,11 @@ __global__ void cuts_kernel(const uint32_t* __restrict__ bin_off, uint32_t log2B
 // small bins inside one window holds < 2W = cap pairs.  Oversize bins
 // (> cap pairs) are listed separately.  item_flag becomes the item id of
 // every bin.  Coalesced tiles with a running carry.
-__global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __restrict__ bin_off, uint32_t log2B,
+__global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __restrict__ bin_off, uint32_t B,
                                                              uint32_t cap, uint32_t* item_flag, uint32_t* items,
                                                              uint32_t* oversize, uint32_t* ctrl) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t carry_sh;
-  const uint32_t B = 1u << log2B;
   const uint32_t W = cap / 2;
   if (threadIdx.x == 0) carry_sh = 0;
   __syncthreads();
@@ -308,7 +306,86 @@ __global__ void __launch_bounds__(kThreads) scatter_kernel(const Pair* __restric
   }
 }
 
+// ---------------------------------------------------------------- many record sets at once
+__device__ __forceinline__ uint32_t upper_set(const uint64_t* __restrict__ off, uint32_t K, uint64_t g) {
+  uint32_t lo = 0, hi = K - 1;  // largest k with off[k] <= g
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Pass A over K record sets: record i of set k goes to global pair slot
+// poff[k] + i with the set's fine bin tbase[k] + q (binary search over the
+// set's own splitters).
+__global__ void __launch_bounds__(kThreads) classify_batch_kernel(const uint8_t* const* __restrict__ ins,
+                                                                  const uint64_t* __restrict__ poff, uint32_t K,
+                                                                  const uint64_t* __restrict__ t,
+                                                                  const uint64_t* __restrict__ tbase,
+                                                                  const uint32_t* __restrict__ log2B,
+                                                                  Pair* __restrict__ pairs, uint32_t* __restrict__ hist) {
+  const uint64_t N = poff[K];
+  for (uint64_t g = blockIdx.x * (uint64_t)kThreads + threadIdx.x; g < N; g += (uint64_t)gridDim.x * kThreads) {
+    const uint32_t k = upper_set(poff, K, g);
+    const uint64_t i = g - poff[k];
+    Pair p = load_pair(ins[k] + i * kRecord, 0);
+    const uint64_t x = enc9_pair(p);
+    const uint64_t* tk = t + tbase[k];
+    uint32_t lo = 0, hi = (1u << log2B[k]) - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (__ldg(tk + mid) <= x) lo = mid;
+      else hi = mid - 1;
+    }
+    const uint32_t q = (uint32_t)tbase[k] + lo;
+    p.lo |= q;
+    pairs[g] = p;
+    atomicAdd(hist + q, 1u);
+  }
+}
+
+// Pass B over K record sets: the pair's index becomes the index within its set.
+__global__ void __launch_bounds__(kThreads) scatter_batch_kernel(const Pair* __restrict__ in,
+                                                                 const uint64_t* __restrict__ poff, uint32_t K,
+                                                                 uint32_t* __restrict__ cursor, Pair* __restrict__ out) {
+  const uint64_t N = poff[K];
+  for (uint64_t g = blockIdx.x * (uint64_t)kThreads + threadIdx.x; g < N; g += (uint64_t)gridDim.x * kThreads) {
+    const Pair p = in[g];
+    const uint32_t slot = atomicAdd(cursor + (uint32_t)p.lo, 1u);
+    const uint32_t k = upper_set(poff, K, g);
+    Pair o;
+    o.hi = p.hi;
+    o.lo = (p.lo & 0xFFFFFFFF00000000ull) | (uint32_t)(g - poff[k]);
+    out[slot] = o;
+  }
+}
+
+// every set's first bin starts a work item (items never span two sets)
+__global__ void mark_set_starts(const uint64_t* __restrict__ tbase, uint32_t K, uint32_t* item_flag) {
+  for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x)
+    item_flag[tbase[k]] = 1u;
+}
+
 }  // namespace
+
+cudaError_t partition_batch(const BatchPartArgs& a) {
+  cudaStream_t st = a.stream;
+  const int sms = sm_count();
+  cudaMemsetAsync(a.cursor, 0, (size_t)a.B * 4, st);
+  cudaMemsetAsync(a.ctrl, 0, 32 * sizeof(uint32_t), st);
+  cudaMemsetAsync(a.item_flag, 0, (size_t)a.B * 4, st);
+  const unsigned grid = (unsigned)sms * 8;
+  classify_batch_kernel<<<grid, kThreads, 0, st>>>(a.ins, a.poff, a.K, a.splitters, a.tbase, a.log2B, a.pairs_in_order,
+                                                  a.cursor);
+  scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
+  scatter_batch_kernel<<<grid, kThreads, 0, st>>>(a.pairs_in_order, a.poff, a.K, a.cursor, a.pairs);
+  mark_set_starts<<<(a.K + 255) / 256, 256, 0, st>>>(a.tbase, a.K, a.item_flag);
+  items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize, a.ctrl);
+  *a.launches += 5;
+  return cudaGetLastError();
+}
 
 cudaError_t partition_records(const PartArgs& a) {
   const uint32_t B = 1u << a.log2B;
@@ -337,7 +414,7 @@ cudaError_t partition_records(const PartArgs& a) {
     classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor);
   }
   if (a.ev[0]) cudaEventRecord(a.ev[0], st);
-  scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.log2B, a.bin_off, a.cursor, a.ctrl);
+  scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, B, a.bin_off, a.cursor, a.ctrl);
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       nullptr);
   if (a.ev[1]) cudaEventRecord(a.ev[1], st);
@@ -355,7 +432,7 @@ cudaError_t build_items(const PartArgs& a) {
   cudaMemsetAsync(a.ctrl, 0, 3 * sizeof(uint32_t), st);  // item count, oversize count, queue head
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       a.item_flag);
-  items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, a.log2B, a.tile_pairs, a.item_flag, a.items, a.oversize,
+  items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, B, a.tile_pairs, a.item_flag, a.items, a.oversize,
                                            a.ctrl);
   *a.launches += 2;
   return cudaGetLastError();

@@ -48,6 +48,11 @@ struct Tile {
 struct KArgs {
   const uint8_t* in;
   uint8_t* out;
+  const uint8_t* const* ins;  // batched path (null for one record set)
+  uint8_t* const* outs;
+  const uint64_t* tbase;
+  const uint64_t* poff;
+  uint32_t K;
   Pair* pairs;
   Pair* temp;
   const uint32_t* bin_off;
@@ -413,10 +418,30 @@ __device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0,
   return src;
 }
 
+__device__ __forceinline__ uint32_t set_of_bin(const uint64_t* __restrict__ tbase, uint32_t K, uint64_t b) {
+  uint32_t lo = 0, hi = K - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (tbase[mid] <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ void process_item(const KArgs& k, const Tile& t, uint32_t it, uint32_t num_items) {
   const uint64_t o0 = k.bin_off[k.items[it]];
   const uint32_t m = k.bin_off[k.items[it + 1]] - (uint32_t)o0;
   if (m == 0) return;
+  // records of this item: one set's buffers (batched path) or the only set
+  const uint8_t* in = k.in;
+  uint8_t* out = k.out;
+  uint64_t base = 0;
+  if (k.ins) {
+    const uint32_t s = set_of_bin(k.tbase, k.K, k.items[it]);
+    in = k.ins[s];
+    out = k.outs[s];
+    base = k.poff[s];
+  }
   if (threadIdx.x == 0 && it + gridDim.x < num_items) {
     // the pairs of the item this CTA will most likely take next: into L2 now
     const uint32_t nx = it + gridDim.x;
@@ -426,10 +451,10 @@ __device__ void process_item(const KArgs& k, const Tile& t, uint32_t it, uint32_
   if (m <= k.cap) {
     load_tile(t, k.pairs + o0, m);
     tile_sort(t, m);
-    gather(k.in, k.out, o0, m, [&](uint32_t j) { return (uint32_t)t.A[t.perm[j]].lo; });
+    gather(in, out, o0 - base, m, [&](uint32_t j) { return (uint32_t)t.A[t.perm[j]].lo; });
   } else {
     const Pair* sorted = sort_oversize(k, t, o0, m);
-    gather(k.in, k.out, o0, m, [&](uint32_t j) { return (uint32_t)sorted[o0 + j].lo; });
+    gather(in, out, o0 - base, m, [&](uint32_t j) { return (uint32_t)sorted[o0 + j].lo; });
   }
   __syncthreads();
 }
@@ -500,10 +525,20 @@ size_t sort_smem_bytes(uint32_t cap) {
   return (size_t)cap * (sizeof(Pair) + 8 + 4 + 2 + 2) + stk * (1 + kWarps) + 16 + sizeof(Misc);
 }
 
+cudaError_t prepare_sort_kernel(uint32_t cap) {
+  return cudaFuncSetAttribute(sort_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)sort_smem_bytes(cap));
+}
+
 cudaError_t sort_items(const SortArgs& a) {
   KArgs k = {};
   k.in = a.records;
   k.out = a.out;
+  k.ins = a.ins;
+  k.outs = a.outs;
+  k.tbase = a.tbase;
+  k.poff = a.poff;
+  k.K = a.K;
   k.pairs = a.pairs;
   k.temp = a.temp;
   k.bin_off = a.bin_off;
@@ -512,8 +547,12 @@ cudaError_t sort_items(const SortArgs& a) {
   k.ctrl = a.ctrl;
   k.cap = a.tile_pairs;
   const size_t smem = sort_smem_bytes(a.tile_pairs);
-  cudaError_t err = cudaFuncSetAttribute(sort_gather_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(a.stream, &cs);
+  if (cs == cudaStreamCaptureStatusNone) {
+    cudaError_t err = prepare_sort_kernel(a.tile_pairs);
+    if (err != cudaSuccess) return err;
+  }
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_gather_kernel, kThreads, smem);
   if (per_sm < 1) per_sm = 1;

@@ -48,7 +48,7 @@ def test_model_bit_identical_to_oracle(name):
     ref = oracle.Rmi(np.sort(oracle.sample(host, S, seed)))
     assert hdr["num_nodes"] == len(ref)
     assert np.array_equal(nodes["s"], ref.s_) and np.array_equal(nodes["e"], ref.e_)
-    assert np.array_equal(nodes["fanout"], ref.fanout) and np.array_equal(nodes["depth"], ref.depth)
+    assert np.array_equal(nodes["fanout"], ref.fanout) and np.array_equal(nodes["depth_set"] & 0xFF, ref.depth)
     inner = ref.fanout > 0
     leaf = ~inner
     assert np.array_equal(nodes["child0"][inner], ref.child0[inner])
