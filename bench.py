@@ -286,6 +286,7 @@ def run_elsar(args):
         e2e = {"value": round(world * bytes_per_step / e2e_s / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": bytes_per_step,
                "steps": args.e2e_steps}
+    batched = None if args.no_batched else run_batched(args, dev, stream)
     if rank != 0:
         return
     cpu = cpu_baseline(args) if world == 1 and not args.no_cpu else None
@@ -298,7 +299,7 @@ def run_elsar(args):
                                    "sets": len(workloads())}),
         "records_per_s": round(world * len(workloads()) * n / (ms / 1e3)),
         "hbm_frac_200B": round(world * len(workloads()) * n * 200 / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "plain": plain,
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "plain": plain, "batched": batched,
         "passes_ms": {"fit": round(pass_ms[0], 3), "classify": round(pass_ms[1], 3),
                       "scan_cuts_items": round(pass_ms[2], 3), "scatter": round(pass_ms[3], 3),
                       "sort_gather": round(sg_ms, 3)},
@@ -307,6 +308,50 @@ def run_elsar(args):
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def run_batched(args, dev, stream):
+    """The batched workload: 4096 record sets of log-uniform size in [1K, 1M]
+    records (scaled so that they hold 4e8 records at most), even sets uniform,
+    odd sets Zipf(1.1) with 5 % duplicates, all sorted by one graph launch."""
+    import torch
+
+    import paper_2305_05671_b300 as elsar
+    import recgen
+
+    sizes = recgen.batch_sizes(args.batch_sets, cap_records=args.batch_cap)
+    d_ins = []
+    for k, n in enumerate(sizes):
+        d = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
+        recgen.generate_gpu(d, n, recgen.batch_spec(k), stream=stream.cuda_stream)
+        d_ins.append(d)
+    d_outs = [torch.empty_like(d) for d in d_ins]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    b = elsar.Batch(d_ins, d_outs, elsar.Params(seed=0x5EED), stream=stream)
+    create_s = time.perf_counter() - t0
+    for _ in range(args.warmup):
+        b.run(stream)
+    b.wait(stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        b.run(stream)
+    ev1.record(stream)
+    b.wait(stream)
+    ms = ev0.elapsed_time(ev1) / args.steps
+    total = sum(sizes)
+    info = b.info()
+    b.close()
+    del d_ins, d_outs
+    torch.cuda.empty_cache()
+    return {"value": round(total * RECORD / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "ms_per_run": round(ms, 3),
+            "sets": len(sizes), "records": total, "graph_launches_per_run": 1,
+            "kernels_in_graph": info["launches"], "tile_pairs": info["tile_pairs"],
+            "records_per_bin_log2_by_class": info["records_per_bin_log2"], "autotune_runs": info["tuning_runs"],
+            "plan_create_s": round(create_s, 2),
+            "workload": "4096 sets, sizes log-uniform in [1K, 1M] records scaled to <= 4e8 records, "
+                        "even sets uniform, odd sets Zipf(1.1) with 5% duplicates"}
 
 
 def main():
@@ -322,6 +367,9 @@ def main():
     ap.add_argument("--records", type=int, default=N_RECORDS, help="records per key set (profiling cases use fewer)")
     ap.add_argument("--sets", default="uniform,zipf", help="key sets to sort per step")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched many-sets workload")
+    ap.add_argument("--batch-sets", type=int, default=4096)
+    ap.add_argument("--batch-cap", type=int, default=400_000_000, help="records across all batched sets")
     args = ap.parse_args()
     global _SETS
     _SETS = tuple(args.sets.split(","))
