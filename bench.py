@@ -268,12 +268,13 @@ def run_elsar(args):
                  "form": "paper partition rule, one sort launch per partition"}
 
     # end to end through elsar_sort_host: pinned host in -> device -> sorted -> pinned host out
-    e2e = None
-    if not args.no_e2e:
+    e2e = ooc = None
+    if not (args.no_e2e and args.no_ooc):
         h_ins = [d.cpu().pin_memory() for d in ins]
         h_out = torch.empty(n * RECORD, dtype=torch.uint8).pin_memory()
         del ins
         torch.cuda.empty_cache()
+    if not args.no_e2e:
         d_in = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
         elsar.sort_host(h_ins[0], h_out, n, p, d_in, out, ws, stream=stream)
         torch.cuda.synchronize()
@@ -286,6 +287,11 @@ def run_elsar(args):
         e2e = {"value": round(world * bytes_per_step / e2e_s / 1e9, 3), "unit": "GB/s",
                "h2d_bytes_per_step": bytes_per_step, "d2h_bytes_per_step": bytes_per_step,
                "steps": args.e2e_steps}
+        del d_in
+    if not args.no_ooc:
+        del ws, out
+        torch.cuda.empty_cache()
+        ooc = run_ooc(args, h_ins, h_out, n, dev, stream)
     batched = None if args.no_batched else run_batched(args, dev, stream)
     if rank != 0:
         return
@@ -300,6 +306,7 @@ def run_elsar(args):
         "records_per_s": round(world * len(workloads()) * n / (ms / 1e3)),
         "hbm_frac_200B": round(world * len(workloads()) * n * 200 / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "plain": plain, "batched": batched,
+        "ooc": ooc,
         "passes_ms": {"fit": round(pass_ms[0], 3), "classify": round(pass_ms[1], 3),
                       "scan_cuts_items": round(pass_ms[2], 3), "scatter": round(pass_ms[3], 3),
                       "sort_gather": round(sg_ms, 3)},
@@ -308,6 +315,58 @@ def run_elsar(args):
         "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
+
+
+def run_ooc(args, h_ins, h_out, n, dev, stream):
+    """Out of core: the same sets held in pinned host memory, sorted into pinned
+    host memory under a device budget well below the data (elsar_sort_ooc).
+    Reports the wall-clock rate, the phase times, the copy volumes and the
+    host link's own bandwidth (one large pinned copy each way) for context."""
+    import torch
+
+    import paper_2305_05671_b300 as elsar
+
+    p = elsar.Params(num_partitions=PARTITIONS, seed=0x5EED)
+    budget = int(args.ooc_budget_gb * (1 << 30))
+    ws = torch.empty(budget, dtype=torch.uint8, device=dev)
+    # the link: one pinned copy of a whole set each way
+    d = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        d.copy_(h_ins[0], non_blocking=True)
+        ev0.record(stream)
+        d.copy_(h_ins[0], non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        h2d_gbs = n * RECORD / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+        ev0.record(stream)
+        h_out.copy_(d, non_blocking=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        d2h_gbs = n * RECORD / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+    del d
+    torch.cuda.empty_cache()
+    elsar.sort_ooc(h_ins[0], h_out, n, p, ws=ws, stream=stream)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sts = [elsar.sort_ooc(h, h_out, n, p, ws=ws, stream=stream) for h in h_ins]
+    wall = time.perf_counter() - t0
+    total = len(h_ins) * n * RECORD
+    h2d = sum(s["h2d_bytes"] for s in sts)
+    d2h = sum(s["d2h_bytes"] for s in sts)
+    # every phase copies whole records; the host-to-device direction carries the most
+    link_bound_s = h2d / (h2d_gbs * 1e9)
+    return {"value": round(total / wall / 1e9, 3), "unit": "GB/s", "wall_s": round(wall, 3),
+            "device_budget_bytes": budget, "data_bytes_per_set": n * RECORD,
+            "phase_ms": {k: [round(s["phase_ms"][i], 1) for s in sts]
+                         for i, k in enumerate(("fit", "count", "split", "sort_groups"))},
+            "h2d_bytes": h2d, "d2h_bytes": d2h, "chunks": [s["chunks"] for s in sts],
+            "groups": [s["groups"] for s in sts], "chunk_records": sts[0]["chunk_records"],
+            "group_records": sts[0]["group_records"], "model_used": [s["model_used"] for s in sts],
+            "link": {"h2d_gbs": round(h2d_gbs, 2), "d2h_gbs": round(d2h_gbs, 2)},
+            "link_bound_frac": round(link_bound_s / wall, 4),
+            "workload": "the step's two sets in pinned host memory, pinned host output, device budget "
+                        f"{args.ooc_budget_gb} GiB"}
 
 
 def run_batched(args, dev, stream):
@@ -369,6 +428,8 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched many-sets workload")
     ap.add_argument("--batch-sets", type=int, default=4096)
+    ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core measurement")
+    ap.add_argument("--ooc-budget-gb", type=float, default=2.0, help="device budget of the out-of-core sort")
     ap.add_argument("--batch-cap", type=int, default=400_000_000, help="records across all batched sets")
     args = ap.parse_args()
     global _SETS

@@ -168,6 +168,41 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
                              void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
 
 /*
+ * Out of core: n records in pinned host memory (h_in, allocated with
+ * cudaHostAlloc / cudaMallocHost or registered with cudaHostRegister, so the
+ * GPU can read it) sorted into h_out (pinned as well, not overlapping h_in)
+ * with no more device memory than the workspace d_ws (ws_bytes is the device
+ * budget).  The paper's external sort (Algorithm 1, Sec. 3.2-3.5) with host
+ * memory in the place of its files:
+ *   fit     the CDF model (model_kind; the network falls back to the RMI as in
+ *           elsar_sort) from a sample read from host memory;
+ *   pass 1  chunks copied in, classified, counted: the exact fine-bin
+ *           histogram gives the partition cuts and the write offsets (Sec. 3.5);
+ *   pass 2  chunks copied in again, split stably by partition on the GPU and
+ *           copied out into their partitions' ranges of h_out, appended in
+ *           input order (the fragment files of Sec. 3.3);
+ *   sort    runs of consecutive partitions that fit the budget are copied in,
+ *           sorted (each run with its own model, as LearnedSort does per
+ *           partition, Sec. 3.4) and copied back in place.
+ * Copies run on side streams overlapped with the kernels.  Synchronises.
+ * Needs ws_bytes >= elsar_ooc_min_workspace(n, p).  A partition larger than
+ * what the budget can sort at once returns ELSAR_EUNSUPPORTED (use more
+ * partitions).  Errors: EINVAL (not pinned host memory, overlap), ENOMEM, ECUDA.
+ */
+typedef struct elsar_ooc_stats {
+  float phase_ms[4];   /* 0 fit, 1 pass 1 (histogram), 2 pass 2 (split), 3 partition sorts */
+  uint64_t h2d_bytes, d2h_bytes;
+  uint32_t chunks, groups;
+  uint64_t chunk_records, group_records;
+  uint32_t model_used, fallback_reason;
+  uint64_t max_partition;
+} elsar_ooc_stats;
+
+size_t elsar_ooc_min_workspace(uint64_t n, const elsar_params* p);
+elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_ws,
+                            size_t ws_bytes, elsar_stream_t stream, elsar_ooc_stats* stats);
+
+/*
  * Many independent record sets in one CUDA-graph-captured launch sequence
  * (the batched form of the method; the paper sorts one file at a time and
  * balances uneven partitions with dynamic thread scheduling, Sec. 7.3 -- here

@@ -47,6 +47,13 @@ class _BatchInfo(ctypes.Structure):
                 ("launches", ctypes.c_uint32), ("tuning_runs", ctypes.c_uint32), ("tuning_ms", ctypes.c_float * 16)]
 
 
+class _OocStats(ctypes.Structure):
+    _fields_ = [("phase_ms", ctypes.c_float * 4), ("h2d_bytes", ctypes.c_uint64), ("d2h_bytes", ctypes.c_uint64),
+                ("chunks", ctypes.c_uint32), ("groups", ctypes.c_uint32), ("chunk_records", ctypes.c_uint64),
+                ("group_records", ctypes.c_uint64), ("model_used", ctypes.c_uint32),
+                ("fallback_reason", ctypes.c_uint32), ("max_partition", ctypes.c_uint64)]
+
+
 @dataclass
 class Params:
     """elsar_params; zero means "library default"."""
@@ -88,6 +95,8 @@ def lib():
             "elsar_sort": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_Stats)]),
             "elsar_sort_host": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
             "elsar_sort_noalloc": (ctypes.c_int, [P, P, U64, PP, P]),
+            "elsar_ooc_min_workspace": (SZ, [U64, PP]),
+            "elsar_sort_ooc": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_OocStats)]),
             "elsar_mlp_grad_workspace": (SZ, [U64]),
             "elsar_mlp_eval": (ctypes.c_int, [P, P, P, U64, P, P]),
             "elsar_mlp_grad": (ctypes.c_int, [P, P, P, P, U64, P, P, SZ, P]),
@@ -200,6 +209,27 @@ def sort_host(h_in, h_out, n: int, p: Params, d_in, d_out, ws, stream=None):
     """Host records in (pinned for async DMA), host records out; synchronises."""
     _check(lib().elsar_sort_host(_ptr(h_in), _ptr(h_out), n, ctypes.byref(p.c()), _ptr(d_in), _ptr(d_out), _ptr(ws),
                                  _nbytes(ws), _stream(stream)))
+
+
+def ooc_min_workspace(n: int, p: Params | None = None) -> int:
+    return int(lib().elsar_ooc_min_workspace(n, ctypes.byref((p or Params()).c())))
+
+
+def sort_ooc(h_in, h_out, n: int, p: Params | None = None, ws=None, budget: int | None = None, stream=None):
+    """Sort n records held in pinned host memory (h_in) into pinned h_out using at
+    most `budget` bytes of device memory (or the given workspace); synchronises and
+    returns the phase statistics."""
+    import torch
+
+    p = p or Params()
+    if ws is None:
+        ws = torch.empty(max(budget or 0, ooc_min_workspace(n, p)), dtype=torch.uint8, device="cuda")
+    st = _OocStats()
+    _check(lib().elsar_sort_ooc(_ptr(h_in), _ptr(h_out), n, ctypes.byref(p.c()), _ptr(ws), _nbytes(ws),
+                                _stream(stream), ctypes.byref(st)))
+    return dict(phase_ms=list(st.phase_ms), h2d_bytes=st.h2d_bytes, d2h_bytes=st.d2h_bytes, chunks=st.chunks,
+                groups=st.groups, chunk_records=st.chunk_records, group_records=st.group_records,
+                model_used=st.model_used, fallback_reason=st.fallback_reason, max_partition=st.max_partition)
 
 
 def mlp_eval(d_w, d_knots, d_x, n: int, d_F, stream=None):

@@ -3,7 +3,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <string>
+#include <vector>
 
 #include "../../include/elsar.h"
 #include "common.cuh"
@@ -553,6 +555,318 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
     return cuda_fail(e, "copy out");
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
   return ELSAR_OK;
+}
+
+// ---------------------------------------------------------------- out of core
+namespace {
+
+constexpr uint64_t kOocChunkMin = 8192;
+// per chunk record: two input buffers, the pairs, the staging copy, the stable rank
+constexpr size_t kOocChunkBytesPerRecord = 2 * 100 + 16 + 100 + 2;
+// per group record: two input and two output buffers
+constexpr size_t kOocGroupBytesPerRecord = 4 * 100;
+constexpr size_t kOocSlack = 64ull << 20;
+
+// device address of pinned host memory, or null when the GPU cannot read it
+const void* device_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+size_t ooc_fixed_bytes(const Resolved& r) {
+  return up((size_t)2 << r.log2B) + up((size_t)4 * r.P) + up((size_t)4 * (r.P + 1)) + 16 * 256;
+}
+
+}  // namespace
+
+extern "C" size_t elsar_ooc_min_workspace(uint64_t n, const elsar_params* p) {
+  Resolved r;
+  if (resolve(n, p, &r) != ELSAR_OK) return 0;
+  return layout(0, r).total + ooc_fixed_bytes(r) + kOocSlack;
+}
+
+extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_ws,
+                                       size_t ws_bytes, elsar_stream_t stream, elsar_ooc_stats* stats) {
+  g_err.clear();
+  Resolved r;
+  elsar_status s = resolve(n, p, &r);
+  if (s != ELSAR_OK) return s;
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n >= (1ull << 32)) return fail(ELSAR_EUNSUPPORTED, "n must be < 2^32");
+  if (n == 0) return ELSAR_OK;
+  if (!d_ws || !aligned(d_ws, 256)) return fail(ELSAR_EINVAL, "workspace must be non-null and 256-byte aligned");
+  const void* dv_in = h_in ? device_view(h_in) : nullptr;
+  if (!dv_in || !h_out || !device_view(h_out))
+    return fail(ELSAR_EINVAL, "h_in and h_out must be pinned host memory the GPU can read");
+  const uint8_t* hi8 = static_cast<const uint8_t*>(h_in);
+  uint8_t* ho8 = static_cast<uint8_t*>(h_out);
+  if (hi8 < ho8 + n * 100 && ho8 < hi8 + n * 100) return fail(ELSAR_EINVAL, "h_in and h_out overlap");
+  if (ws_bytes < elsar_ooc_min_workspace(n, p)) return fail(ELSAR_ENOMEM, "workspace below elsar_ooc_min_workspace");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the model and its scratch first; the chunk buffers, later the group buffers, after it
+  const Layout Lf = layout(0, r);
+  uint8_t* rest = static_cast<uint8_t*>(d_ws) + Lf.total;
+  const size_t rest_bytes = ws_bytes - Lf.total;
+
+  // side streams for the copies; events order them against the kernels on st
+  cudaStream_t up_st = nullptr, down_st = nullptr;
+  cudaEvent_t ev_t[5] = {}, in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {}, stage_free = nullptr;
+  cudaError_t e = cudaStreamCreateWithFlags(&up_st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&down_st, cudaStreamNonBlocking);
+  for (auto& ev : ev_t)
+    if (e == cudaSuccess) e = cudaEventCreate(&ev);
+  for (int i = 0; i < 2; ++i) {
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in_ready[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&in_free[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out_ready[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out_free[i], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&stage_free, cudaEventDisableTiming);
+  auto cleanup = [&]() {
+    if (up_st) cudaStreamSynchronize(up_st);
+    if (down_st) cudaStreamSynchronize(down_st);
+    for (auto* ev : {&ev_t[0], &ev_t[1], &ev_t[2], &ev_t[3], &ev_t[4], &in_ready[0], &in_ready[1], &in_free[0],
+                     &in_free[1], &out_ready[0], &out_ready[1], &out_free[0], &out_free[1], &stage_free})
+      if (*ev) cudaEventDestroy(*ev);
+    if (up_st) cudaStreamDestroy(up_st);
+    if (down_st) cudaStreamDestroy(down_st);
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return cuda_fail(e, "out-of-core setup");
+  }
+  cudaEventRecord(ev_t[0], st);
+  uint64_t h2d = 0, d2h = 0;
+
+  // ---- fit: the sample is read straight from host memory
+  uint32_t launches = 0;
+  FitResult fr;
+  void* model = at<void>(d_ws, Lf.model);
+  s = do_fit(dv_in, n, r, model, d_ws, Lf, st, &launches, &fr);
+  if (s != ELSAR_OK) {
+    cleanup();
+    return s;
+  }
+  cudaEventRecord(ev_t[1], st);
+
+  // ---- chunk buffers
+  const size_t fixed = ooc_fixed_bytes(r);
+  const size_t per_rec = kOocChunkBytesPerRecord + ((size_t)4 * r.P + 8191) / 8192;
+  uint64_t C = rest_bytes > fixed ? (rest_bytes - fixed) / per_rec : 0;
+  C = (C / kOocChunkMin) * kOocChunkMin;
+  C = std::min<uint64_t>(C, ((n + kOocChunkMin - 1) / kOocChunkMin) * kOocChunkMin);
+  C = std::min<uint64_t>(C, 1ull << 30);
+  if (C < kOocChunkMin) {
+    cleanup();
+    return fail(ELSAR_ENOMEM, "device budget too small for a chunk of records");
+  }
+  size_t o = 0;
+  auto carve = [&](size_t bytes) {
+    uint8_t* q = rest + o;
+    o += up(bytes);
+    return q;
+  };
+  uint8_t* cbuf[2] = {carve(C * 100), carve(C * 100)};
+  Pair* cpairs = reinterpret_cast<Pair*>(carve(C * 16));
+  uint8_t* stage = carve(C * 100);
+  uint16_t* rank = reinterpret_cast<uint16_t*>(carve(C * 2));
+  uint32_t* tile_hist = reinterpret_cast<uint32_t*>(carve(ooc_tiles(C) * r.P * 4));
+  uint32_t* pcount = reinterpret_cast<uint32_t*>(carve((size_t)r.P * 4));
+  uint32_t* poff_chunk = reinterpret_cast<uint32_t*>(carve((size_t)(r.P + 1) * 4));
+  uint16_t* b2p = reinterpret_cast<uint16_t*>(carve((size_t)2 << r.log2B));
+  if (o > rest_bytes) {
+    cleanup();
+    return fail(ELSAR_ENOMEM, "device budget too small for the chunk buffers");
+  }
+  PartArgs a = part_args(model, nullptr, 0, r, nullptr, at<uint32_t>(d_ws, Lf.bin_off),
+                         at<uint64_t>(d_ws, Lf.part_off), d_ws, Lf, st, &launches);
+  a.pairs_in_order = cpairs;
+  const uint64_t nchunks = (n + C - 1) / C;
+  std::vector<uint64_t> part_off(r.P + 1), filled(r.P, 0);
+  std::vector<uint32_t> coff(r.P + 1);
+  auto issue_in = [&](uint64_t c) {
+    const int b = (int)(c & 1);
+    const uint64_t cn = std::min<uint64_t>(C, n - c * C);
+    cudaStreamWaitEvent(up_st, in_free[b], 0);
+    cudaMemcpyAsync(cbuf[b], hi8 + c * C * 100, cn * 100, cudaMemcpyHostToDevice, up_st);
+    cudaEventRecord(in_ready[b], up_st);
+    h2d += cn * 100;
+  };
+  // pass 1 counts (and runs again if the network's partitions fail the
+  // full-data check and the RMI takes over); pass 2 splits and copies out
+  int pass = 0;
+  while (pass < 2 && s == ELSAR_OK) {
+    if (pass == 0) {
+      cudaMemsetAsync(a.cursor, 0, (size_t)4 << r.log2B, st);  // the histogram
+      cudaMemsetAsync(a.ctrl, 0, 32 * sizeof(uint32_t), st);
+    }
+    for (int b = 0; b < 2; ++b) cudaEventRecord(in_free[b], st);
+    cudaEventRecord(stage_free, st);
+    issue_in(0);
+    for (uint64_t c = 0; c < nchunks && s == ELSAR_OK; ++c) {
+      const int b = (int)(c & 1);
+      const uint64_t cn = std::min<uint64_t>(C, n - c * C);
+      if (c + 1 < nchunks) issue_in(c + 1);
+      cudaStreamWaitEvent(st, in_ready[b], 0);
+      a.records = cbuf[b];
+      a.n = cn;
+      if ((e = classify_accumulate(a)) != cudaSuccess) {
+        s = cuda_fail(e, "out-of-core classify");
+        break;
+      }
+      if (pass == 0) {
+        cudaEventRecord(in_free[b], st);
+        continue;
+      }
+      cudaStreamWaitEvent(st, stage_free, 0);
+      e = ooc_split_chunk(cbuf[b], cn, cpairs, b2p, r.P, tile_hist, rank, pcount, poff_chunk, stage, st);
+      launches += 4;
+      cudaEventRecord(in_free[b], st);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(coff.data(), poff_chunk, (r.P + 1) * 4, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        s = cuda_fail(e, "out-of-core split");
+        break;
+      }
+      // each partition's piece of this chunk is appended to its range of h_out
+      for (uint32_t q = 0; q < r.P; ++q) {
+        const uint64_t cnt = coff[q + 1] - coff[q];
+        if (!cnt) continue;
+        if (filled[q] + cnt > part_off[q + 1] - part_off[q]) {
+          s = fail(ELSAR_ECUDA, "out-of-core split: partition %u overflows its counted range", q);
+          break;
+        }
+        cudaMemcpyAsync(ho8 + (part_off[q] + filled[q]) * 100, stage + (uint64_t)coff[q] * 100, cnt * 100,
+                        cudaMemcpyDeviceToHost, down_st);
+        filled[q] += cnt;
+        d2h += cnt * 100;
+      }
+      cudaEventRecord(stage_free, down_st);
+    }
+    if (s != ELSAR_OK) break;
+    if (pass == 0) {
+      // the exact histogram gives the cuts and the write offsets (Sec. 3.5)
+      e = scan_and_cut(a);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(part_off.data(), a.part_off, (r.P + 1) * 8, cudaMemcpyDeviceToHost, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+      if (e != cudaSuccess) {
+        s = cuda_fail(e, "out-of-core cuts");
+        break;
+      }
+      uint64_t mx = 0;
+      for (uint32_t q = 0; q < r.P; ++q) mx = std::max<uint64_t>(mx, part_off[q + 1] - part_off[q]);
+      if (fr.kind == ELSAR_MODEL_MLP && (double)mx * r.P > 1.1 * (double)n) {
+        fr.kind = ELSAR_MODEL_RMI;
+        fr.fallback = 3;
+        s = revert_to_rmi(model, r, d_ws, Lf, st, 3);
+        continue;  // count again with the RMI's splitters
+      }
+      if ((e = ooc_bin_to_part(a.cuts, r.P, 1u << r.log2B, b2p, st)) != cudaSuccess) {
+        s = cuda_fail(e, "out-of-core partition map");
+        break;
+      }
+      cudaEventRecord(ev_t[2], st);
+    }
+    ++pass;
+  }
+  if (s == ELSAR_OK) {
+    e = cudaStreamSynchronize(down_st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(up_st);
+    if (e != cudaSuccess) s = cuda_fail(e, "out-of-core copy out");
+  }
+  if (s == ELSAR_OK) {
+    for (uint32_t q = 0; q < r.P && s == ELSAR_OK; ++q)
+      if (filled[q] != part_off[q + 1] - part_off[q])
+        s = fail(ELSAR_ECUDA, "out-of-core split: partition %u got %llu of %llu records", q,
+                 (unsigned long long)filled[q], (unsigned long long)(part_off[q + 1] - part_off[q]));
+  }
+  if (s == ELSAR_OK) s = device_status(d_ws, Lf, st);
+  cudaEventRecord(ev_t[3], st);
+
+  // ---- runs of consecutive partitions that fit the budget: in, sorted, back in place
+  elsar_params gp;
+  if (p) gp = *p;
+  else elsar_default_params(&gp);
+  gp.model_kind = ELSAR_MODEL_RMI;
+  gp.sample_size = 0;
+  gp.fine_bins_log2 = 0;
+  gp.num_partitions = 0;
+  uint64_t G = (rest_bytes / (kOocGroupBytesPerRecord + 64)) & ~63ull;
+  while (G > 0 && kOocGroupBytesPerRecord * G + 256 + elsar_workspace_size(G, &gp) > rest_bytes)
+    G = (G * 15 / 16) & ~63ull;
+  uint64_t maxpart = 0;
+  for (uint32_t q = 0; q < r.P; ++q) maxpart = std::max<uint64_t>(maxpart, part_off[q + 1] - part_off[q]);
+  if (s == ELSAR_OK && maxpart > G)
+    s = fail(ELSAR_EUNSUPPORTED, "a partition of %llu records exceeds the %llu the device budget sorts at once",
+             (unsigned long long)maxpart, (unsigned long long)G);
+  uint32_t groups = 0;
+  if (s == ELSAR_OK) {
+    uint8_t* gin[2] = {rest, rest + G * 100};
+    uint8_t* gout[2] = {rest + 2 * G * 100, rest + 3 * G * 100};
+    uint8_t* gws = rest + up(4 * G * 100);
+    const size_t gws_bytes = rest_bytes - up(4 * G * 100);
+    std::vector<uint64_t> gb(1, 0);  // group boundaries in records
+    for (uint32_t q = 0; q < r.P;) {
+      const uint64_t start = part_off[q];
+      while (q < r.P && part_off[q + 1] - start <= G) ++q;
+      gb.push_back(part_off[q]);
+    }
+    for (int b = 0; b < 2; ++b) {
+      cudaEventRecord(in_free[b], st);
+      cudaEventRecord(out_free[b], st);
+    }
+    auto group_in = [&](size_t g) {
+      const int b = (int)(g & 1);
+      const uint64_t m = gb[g + 1] - gb[g];
+      cudaStreamWaitEvent(up_st, in_free[b], 0);
+      cudaMemcpyAsync(gin[b], ho8 + gb[g] * 100, m * 100, cudaMemcpyHostToDevice, up_st);
+      cudaEventRecord(in_ready[b], up_st);
+      h2d += m * 100;
+    };
+    const size_t ng = gb.size() - 1;
+    group_in(0);
+    for (size_t g = 0; g < ng && s == ELSAR_OK; ++g) {
+      const int b = (int)(g & 1);
+      const uint64_t m = gb[g + 1] - gb[g];
+      if (g + 1 < ng) group_in(g + 1);
+      cudaStreamWaitEvent(st, in_ready[b], 0);
+      cudaStreamWaitEvent(st, out_free[b], 0);
+      s = elsar_sort(gin[b], gout[b], m, &gp, gws, gws_bytes, stream, nullptr);
+      if (s != ELSAR_OK) break;
+      cudaEventRecord(in_free[b], st);
+      cudaEventRecord(out_ready[b], st);
+      cudaStreamWaitEvent(down_st, out_ready[b], 0);
+      cudaMemcpyAsync(ho8 + gb[g] * 100, gout[b], m * 100, cudaMemcpyDeviceToHost, down_st);
+      cudaEventRecord(out_free[b], down_st);
+      d2h += m * 100;
+      ++groups;
+    }
+    if (s == ELSAR_OK) {
+      e = cudaStreamSynchronize(down_st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(up_st);
+      if (e != cudaSuccess) s = cuda_fail(e, "out-of-core group copies");
+    }
+  }
+  cudaEventRecord(ev_t[4], st);
+  if (s == ELSAR_OK && (e = cudaEventSynchronize(ev_t[4])) != cudaSuccess) s = cuda_fail(e, "out-of-core");
+  if (s == ELSAR_OK && stats) {
+    for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&stats->phase_ms[i], ev_t[i], ev_t[i + 1]);
+    stats->h2d_bytes = h2d;
+    stats->d2h_bytes = d2h;
+    stats->chunks = (uint32_t)nchunks;
+    stats->groups = groups;
+    stats->chunk_records = C;
+    stats->group_records = G;
+    stats->model_used = fr.kind;
+    stats->fallback_reason = fr.fallback;
+    stats->max_partition = maxpart;
+  }
+  cleanup();
+  return s;
 }
 
 size_t elsar_mlp_grad_workspace(uint64_t n) {

@@ -290,6 +290,17 @@ struct SortArgs {
 };
 
 cudaError_t sort_items(const SortArgs& a);
+
+// out-of-core helpers (ooc.cu)
+uint64_t ooc_tiles(uint64_t n);
+cudaError_t ooc_bin_to_part(const uint32_t* cuts, uint32_t P, uint32_t B, uint16_t* lut, cudaStream_t st);
+cudaError_t ooc_split_chunk(const uint8_t* d_chunk, uint64_t n, const Pair* pairs, const uint16_t* lut, uint32_t P,
+                            uint32_t* tile_hist, uint16_t* rank, uint32_t* part_count, uint32_t* part_off,
+                            uint8_t* d_staging, cudaStream_t st);
+// classify a chunk into input-order pairs (fine bin in the pair) and add to hist
+cudaError_t classify_accumulate(const PartArgs& a);
+// scan of the histogram and partition cuts
+cudaError_t scan_and_cut(const PartArgs& a);
 cudaError_t prepare_sort_kernel(uint32_t cap);  // kernel attributes, before any stream capture
 int sm_count();
 

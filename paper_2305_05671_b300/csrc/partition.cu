@@ -425,6 +425,36 @@ cudaError_t partition_records(const PartArgs& a) {
   return cudaGetLastError();
 }
 
+cudaError_t classify_accumulate(const PartArgs& a) {
+  cudaStream_t st = a.stream;
+  const int sms = sm_count();
+  Pair* pin = static_cast<Pair*>(a.pairs_in_order);
+  if ((reinterpret_cast<uintptr_t>(a.records) & 15) == 0) {
+    const size_t smem = (size_t)kStages * kTileBytes;
+    cudaFuncSetAttribute(classify_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_tma_kernel, kThreads, smem);
+    const uint64_t tiles = a.n / kTileRecs;
+    const unsigned grid = (unsigned)umax64(1, umin64(tiles, (uint64_t)sms * (occ > 0 ? occ : 1)));
+    classify_tma_kernel<<<grid, kThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl);
+  } else {
+    const uint64_t per_block = (uint64_t)kThreads * kUnroll;
+    const unsigned grid = (unsigned)umax64(1, umin64((a.n + per_block - 1) / per_block, (uint64_t)sms * 4));
+    classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor);
+  }
+  *a.launches += 1;
+  return cudaGetLastError();
+}
+
+cudaError_t scan_and_cut(const PartArgs& a) {
+  const uint32_t B = 1u << a.log2B;
+  scan_bins<<<1, kScanThreads, 0, a.stream>>>(a.cursor, B, a.bin_off, a.cursor, a.ctrl);
+  cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, a.stream>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts,
+                                                           a.part_off, nullptr);
+  *a.launches += 2;
+  return cudaGetLastError();
+}
+
 cudaError_t build_items(const PartArgs& a) {
   cudaStream_t st = a.stream;
   const uint32_t B = 1u << a.log2B;
