@@ -561,8 +561,8 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
 namespace {
 
 constexpr uint64_t kOocChunkMin = 8192;
-// per chunk record: two input buffers, the pairs, the staging copy, the stable rank
-constexpr size_t kOocChunkBytesPerRecord = 2 * 100 + 16 + 100 + 2;
+// per chunk record: two input buffers, the pairs, two staging buffers, the stable rank
+constexpr size_t kOocChunkBytesPerRecord = 2 * 100 + 16 + 2 * 100 + 2;
 // per group record: two input and two output buffers
 constexpr size_t kOocGroupBytesPerRecord = 4 * 100;
 constexpr size_t kOocSlack = 64ull << 20;
@@ -578,7 +578,8 @@ const void* device_view(const void* p) {
 }
 
 size_t ooc_fixed_bytes(const Resolved& r) {
-  return up((size_t)2 << r.log2B) + up((size_t)4 * r.P) + up((size_t)4 * (r.P + 1)) + 16 * 256;
+  return up((size_t)2 << r.log2B) + up((size_t)4 * r.P) + 2 * up((size_t)4 * (r.P + 1)) + 3 * up((size_t)8 * r.P) +
+         16 * 256;
 }
 
 }  // namespace
@@ -600,7 +601,8 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
   if (n == 0) return ELSAR_OK;
   if (!d_ws || !aligned(d_ws, 256)) return fail(ELSAR_EINVAL, "workspace must be non-null and 256-byte aligned");
   const void* dv_in = h_in ? device_view(h_in) : nullptr;
-  if (!dv_in || !h_out || !device_view(h_out))
+  uint8_t* dv_out = h_out ? static_cast<uint8_t*>(const_cast<void*>(device_view(h_out))) : nullptr;
+  if (!dv_in || !dv_out)
     return fail(ELSAR_EINVAL, "h_in and h_out must be pinned host memory the GPU can read");
   const uint8_t* hi8 = static_cast<const uint8_t*>(h_in);
   uint8_t* ho8 = static_cast<uint8_t*>(h_out);
@@ -614,7 +616,7 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
 
   // side streams for the copies; events order them against the kernels on st
   cudaStream_t up_st = nullptr, down_st = nullptr;
-  cudaEvent_t ev_t[5] = {}, in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {}, stage_free = nullptr;
+  cudaEvent_t ev_t[5] = {}, in_ready[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
   cudaError_t e = cudaStreamCreateWithFlags(&up_st, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&down_st, cudaStreamNonBlocking);
   for (auto& ev : ev_t)
@@ -625,12 +627,11 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out_ready[i], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&out_free[i], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&stage_free, cudaEventDisableTiming);
   auto cleanup = [&]() {
     if (up_st) cudaStreamSynchronize(up_st);
     if (down_st) cudaStreamSynchronize(down_st);
     for (auto* ev : {&ev_t[0], &ev_t[1], &ev_t[2], &ev_t[3], &ev_t[4], &in_ready[0], &in_ready[1], &in_free[0],
-                     &in_free[1], &out_ready[0], &out_ready[1], &out_free[0], &out_free[1], &stage_free})
+                     &in_free[1], &out_ready[0], &out_ready[1], &out_free[0], &out_free[1]})
       if (*ev) cudaEventDestroy(*ev);
     if (up_st) cudaStreamDestroy(up_st);
     if (down_st) cudaStreamDestroy(down_st);
@@ -672,12 +673,16 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
   };
   uint8_t* cbuf[2] = {carve(C * 100), carve(C * 100)};
   Pair* cpairs = reinterpret_cast<Pair*>(carve(C * 16));
-  uint8_t* stage = carve(C * 100);
+  uint8_t* stage[2] = {carve(C * 100), carve(C * 100)};
   uint16_t* rank = reinterpret_cast<uint16_t*>(carve(C * 2));
   uint32_t* tile_hist = reinterpret_cast<uint32_t*>(carve(ooc_tiles(C) * r.P * 4));
   uint32_t* pcount = reinterpret_cast<uint32_t*>(carve((size_t)r.P * 4));
-  uint32_t* poff_chunk = reinterpret_cast<uint32_t*>(carve((size_t)(r.P + 1) * 4));
+  uint32_t* poff_chunk[2] = {reinterpret_cast<uint32_t*>(carve((size_t)(r.P + 1) * 4)),
+                             reinterpret_cast<uint32_t*>(carve((size_t)(r.P + 1) * 4))};
   uint16_t* b2p = reinterpret_cast<uint16_t*>(carve((size_t)2 << r.log2B));
+  uint64_t* dst_next = reinterpret_cast<uint64_t*>(carve((size_t)8 * r.P));
+  uint64_t* dst_cur[2] = {reinterpret_cast<uint64_t*>(carve((size_t)8 * r.P)),
+                          reinterpret_cast<uint64_t*>(carve((size_t)8 * r.P))};
   if (o > rest_bytes) {
     cleanup();
     return fail(ELSAR_ENOMEM, "device budget too small for the chunk buffers");
@@ -686,8 +691,17 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
                          at<uint64_t>(d_ws, Lf.part_off), d_ws, Lf, st, &launches);
   a.pairs_in_order = cpairs;
   const uint64_t nchunks = (n + C - 1) / C;
-  std::vector<uint64_t> part_off(r.P + 1), filled(r.P, 0);
-  std::vector<uint32_t> coff(r.P + 1);
+  std::vector<uint64_t> part_off(r.P + 1);
+  OocSplitArgs sa = {};
+  sa.lut = b2p;
+  sa.pairs = cpairs;
+  sa.P = r.P;
+  sa.tile_hist = tile_hist;
+  sa.rank = rank;
+  sa.part_count = pcount;
+  sa.dst_next = dst_next;
+  sa.part_end = a.part_off + 1;
+  sa.out = dv_out;
   auto issue_in = [&](uint64_t c) {
     const int b = (int)(c & 1);
     const uint64_t cn = std::min<uint64_t>(C, n - c * C);
@@ -703,9 +717,13 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
     if (pass == 0) {
       cudaMemsetAsync(a.cursor, 0, (size_t)4 << r.log2B, st);  // the histogram
       cudaMemsetAsync(a.ctrl, 0, 32 * sizeof(uint32_t), st);
+    } else {
+      cudaMemcpyAsync(dst_next, a.part_off, (size_t)8 * r.P, cudaMemcpyDeviceToDevice, st);
     }
-    for (int b = 0; b < 2; ++b) cudaEventRecord(in_free[b], st);
-    cudaEventRecord(stage_free, st);
+    for (int b = 0; b < 2; ++b) {
+      cudaEventRecord(in_free[b], st);
+      cudaEventRecord(out_free[b], st);
+    }
     issue_in(0);
     for (uint64_t c = 0; c < nchunks && s == ELSAR_OK; ++c) {
       const int b = (int)(c & 1);
@@ -718,34 +736,31 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
         s = cuda_fail(e, "out-of-core classify");
         break;
       }
-      if (pass == 0) {
-        cudaEventRecord(in_free[b], st);
-        continue;
-      }
-      cudaStreamWaitEvent(st, stage_free, 0);
-      e = ooc_split_chunk(cbuf[b], cn, cpairs, b2p, r.P, tile_hist, rank, pcount, poff_chunk, stage, st);
-      launches += 4;
-      cudaEventRecord(in_free[b], st);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(coff.data(), poff_chunk, (r.P + 1) * 4, cudaMemcpyDeviceToHost, st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) {
-        s = cuda_fail(e, "out-of-core split");
-        break;
-      }
-      // each partition's piece of this chunk is appended to its range of h_out
-      for (uint32_t q = 0; q < r.P; ++q) {
-        const uint64_t cnt = coff[q + 1] - coff[q];
-        if (!cnt) continue;
-        if (filled[q] + cnt > part_off[q + 1] - part_off[q]) {
-          s = fail(ELSAR_ECUDA, "out-of-core split: partition %u overflows its counted range", q);
+      if (pass == 1) {
+        // stable split by partition into stage[b] (free once its previous
+        // copy-out ended), then on the copy stream every piece appended to
+        // its partition's range of h_out while the next chunk is split
+        sa.chunk = cbuf[b];
+        sa.n = cn;
+        sa.stage = stage[b];
+        sa.chunk_off = poff_chunk[b];
+        sa.dst_cur = dst_cur[b];
+        cudaStreamWaitEvent(st, out_free[b], 0);
+        if ((e = ooc_split_chunk(sa, st)) != cudaSuccess) {
+          s = cuda_fail(e, "out-of-core split");
           break;
         }
-        cudaMemcpyAsync(ho8 + (part_off[q] + filled[q]) * 100, stage + (uint64_t)coff[q] * 100, cnt * 100,
-                        cudaMemcpyDeviceToHost, down_st);
-        filled[q] += cnt;
-        d2h += cnt * 100;
+        cudaEventRecord(out_ready[b], st);
+        cudaStreamWaitEvent(down_st, out_ready[b], 0);
+        if ((e = ooc_copy_out(sa, down_st)) != cudaSuccess) {
+          s = cuda_fail(e, "out-of-core copy-out");
+          break;
+        }
+        cudaEventRecord(out_free[b], down_st);
+        launches += 5;
+        d2h += cn * 100;
       }
-      cudaEventRecord(stage_free, down_st);
+      cudaEventRecord(in_free[b], st);
     }
     if (s != ELSAR_OK) break;
     if (pass == 0) {
@@ -779,10 +794,15 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
     if (e != cudaSuccess) s = cuda_fail(e, "out-of-core copy out");
   }
   if (s == ELSAR_OK) {
+    // every partition's range must have been filled exactly
+    std::vector<uint64_t> next(r.P);
+    e = cudaMemcpyAsync(next.data(), dst_next, (size_t)8 * r.P, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) s = cuda_fail(e, "out-of-core split check");
     for (uint32_t q = 0; q < r.P && s == ELSAR_OK; ++q)
-      if (filled[q] != part_off[q + 1] - part_off[q])
+      if (next[q] != part_off[q + 1])
         s = fail(ELSAR_ECUDA, "out-of-core split: partition %u got %llu of %llu records", q,
-                 (unsigned long long)filled[q], (unsigned long long)(part_off[q + 1] - part_off[q]));
+                 (unsigned long long)(next[q] - part_off[q]), (unsigned long long)(part_off[q + 1] - part_off[q]));
   }
   if (s == ELSAR_OK) s = device_status(d_ws, Lf, st);
   cudaEventRecord(ev_t[3], st);

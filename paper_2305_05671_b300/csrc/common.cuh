@@ -294,9 +294,26 @@ cudaError_t sort_items(const SortArgs& a);
 // out-of-core helpers (ooc.cu)
 uint64_t ooc_tiles(uint64_t n);
 cudaError_t ooc_bin_to_part(const uint32_t* cuts, uint32_t P, uint32_t B, uint16_t* lut, cudaStream_t st);
-cudaError_t ooc_split_chunk(const uint8_t* d_chunk, uint64_t n, const Pair* pairs, const uint16_t* lut, uint32_t P,
-                            uint32_t* tile_hist, uint16_t* rank, uint32_t* part_count, uint32_t* part_off,
-                            uint8_t* d_staging, cudaStream_t st);
+struct OocSplitArgs {
+  const uint8_t* chunk;      // the chunk's records (device)
+  uint64_t n;                // records in the chunk
+  const Pair* pairs;         // the chunk's pairs in input order, fine bin in lo
+  const uint16_t* lut;       // fine bin -> partition
+  uint32_t P;
+  uint32_t* tile_hist;       // ooc_tiles(n) x P
+  uint16_t* rank;            // n
+  uint32_t* part_count;      // P
+  uint32_t* chunk_off;       // P + 1: partition starts inside the chunk
+  uint8_t* stage;            // n records, the chunk in partition order
+  uint64_t* dst_next;        // P: next free output record of every partition
+  uint64_t* dst_cur;         // P: this chunk's destination of every partition
+  const uint64_t* part_end;  // P: end of every partition's output range (records)
+  uint8_t* out;              // the output records (host memory mapped into the device)
+};
+// stable split of a chunk by partition into `stage`
+cudaError_t ooc_split_chunk(const OocSplitArgs& a, cudaStream_t st);
+// every partition's piece of `stage` appended to its output range
+cudaError_t ooc_copy_out(const OocSplitArgs& a, cudaStream_t st);
 // classify a chunk into input-order pairs (fine bin in the pair) and add to hist
 cudaError_t classify_accumulate(const PartArgs& a);
 // scan of the histogram and partition cuts

@@ -84,9 +84,12 @@ __global__ void column_scan_kernel(uint32_t* __restrict__ tile_hist, uint32_t ti
   }
 }
 
-// single CTA: exclusive scan of the chunk's partition counts
+// single CTA: exclusive scan of the chunk's partition counts; every
+// partition's destination for this chunk (dst_cur) is where the previous
+// chunks left off (dst_next), which then advances by the chunk's count
 __global__ void __launch_bounds__(1024) part_scan_kernel(const uint32_t* __restrict__ cnt, uint32_t P,
-                                                         uint32_t* __restrict__ off) {
+                                                         uint32_t* __restrict__ off, uint64_t* __restrict__ dst_next,
+                                                         uint64_t* __restrict__ dst_cur) {
   __shared__ uint32_t wsum[32];
   __shared__ uint32_t carry;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -113,7 +116,12 @@ __global__ void __launch_bounds__(1024) part_scan_kernel(const uint32_t* __restr
     }
     __syncthreads();
     const uint32_t c = carry;
-    if (p < P) off[p] = c + wsum[warp] + incl - v;
+    if (p < P) {
+      off[p] = c + wsum[warp] + incl - v;
+      const uint64_t d = dst_next[p];
+      dst_cur[p] = d;
+      dst_next[p] = d + v;
+    }
     __syncthreads();
     if (threadIdx.x == 1023) carry = c + wsum[warp] + incl;
     __syncthreads();
@@ -151,6 +159,45 @@ __global__ void split_records_kernel(const uint8_t* __restrict__ in, uint64_t n,
   }
 }
 
+// the partition-ordered chunk to its partitions' ranges of the output (host
+// memory mapped into the device's address space): record j of the chunk
+// belongs to the last q with off[q] <= j and goes to dst_cur[q] + j - off[q];
+// consecutive records of a partition land next to each other, so a warp's
+// stores form long contiguous runs.  A destination at or past the
+// partition's end (part_end[q]) is not written; the caller checks the counts.
+__global__ void copy_out_kernel(const uint8_t* __restrict__ stage, uint64_t n, const uint32_t* __restrict__ off,
+                                uint32_t P, const uint64_t* __restrict__ dst_cur, const uint64_t* __restrict__ part_end,
+                                uint8_t* __restrict__ out) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  const uint32_t* in32 = reinterpret_cast<const uint32_t*>(stage);
+  uint32_t* out32 = reinterpret_cast<uint32_t*>(out);
+  for (uint64_t g = blockIdx.x * (uint64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); g * 32 < n; g += warps) {
+    const uint64_t j = g * 32 + lane;
+    uint64_t dst = 0;
+    uint32_t ok = 0;
+    if (j < n) {
+      uint32_t lo = 0, hi = P - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= j) lo = mid;
+        else hi = mid - 1;
+      }
+      dst = dst_cur[lo] + (j - off[lo]);
+      ok = dst < part_end[lo];
+    }
+    const uint32_t nrec = (uint32_t)min((uint64_t)32, n - g * 32);
+#pragma unroll 5
+    for (uint32_t k0 = 0; k0 < 25u; ++k0) {
+      const uint32_t w = k0 * 32u + lane;
+      const uint32_t r = w / 25u, k = w - 25u * r;
+      const uint64_t d = __shfl_sync(0xffffffffu, dst, r);
+      const uint32_t okr = __shfl_sync(0xffffffffu, ok, r);
+      if (r < nrec && okr) out32[d * 25u + k] = in32[(g * 32 + r) * 25u + k];
+    }
+  }
+}
+
 }  // namespace
 
 uint64_t ooc_tiles(uint64_t n) { return (n + kTile - 1) / kTile; }
@@ -161,16 +208,24 @@ cudaError_t ooc_bin_to_part(const uint32_t* cuts, uint32_t P, uint32_t B, uint16
   return cudaGetLastError();
 }
 
-cudaError_t ooc_split_chunk(const uint8_t* d_chunk, uint64_t n, const Pair* pairs, const uint16_t* lut, uint32_t P,
-                            uint32_t* tile_hist, uint16_t* rank, uint32_t* part_count, uint32_t* part_off,
-                            uint8_t* d_staging, cudaStream_t st) {
-  const uint64_t tiles = ooc_tiles(n);
-  if (!n) return cudaSuccess;
-  tile_split_kernel<<<(unsigned)tiles, kTileThreads, 0, st>>>(pairs, n, lut, P, tile_hist, rank);
-  column_scan_kernel<<<(P + 255) / 256, 256, 0, st>>>(tile_hist, (uint32_t)tiles, P, part_count);
-  part_scan_kernel<<<1, 1024, 0, st>>>(part_count, P, part_off);
-  const unsigned grid = (unsigned)min((uint64_t)sm_count() * 16, (n + 255) / 256 + 1);
-  split_records_kernel<<<grid, 256, 0, st>>>(d_chunk, n, pairs, lut, tile_hist, part_off, rank, P, d_staging);
+cudaError_t ooc_split_chunk(const OocSplitArgs& a, cudaStream_t st) {
+  if (!a.n) return cudaSuccess;
+  const uint64_t tiles = ooc_tiles(a.n);
+  tile_split_kernel<<<(unsigned)tiles, kTileThreads, 0, st>>>(a.pairs, a.n, a.lut, a.P, a.tile_hist, a.rank);
+  column_scan_kernel<<<(a.P + 255) / 256, 256, 0, st>>>(a.tile_hist, (uint32_t)tiles, a.P, a.part_count);
+  part_scan_kernel<<<1, 1024, 0, st>>>(a.part_count, a.P, a.chunk_off, a.dst_next, a.dst_cur);
+  const unsigned grid = (unsigned)min((uint64_t)sm_count() * 16, (a.n + 255) / 256 + 1);
+  split_records_kernel<<<grid, 256, 0, st>>>(a.chunk, a.n, a.pairs, a.lut, a.tile_hist, a.chunk_off, a.rank, a.P,
+                                             a.stage);
+  return cudaGetLastError();
+}
+
+cudaError_t ooc_copy_out(const OocSplitArgs& a, cudaStream_t st) {
+  if (!a.n) return cudaSuccess;
+  // stores to host memory need few warps to keep the link busy; leave the
+  // rest of the GPU to the next chunk's kernels on the other stream
+  const unsigned grid = (unsigned)min((uint64_t)sm_count() * 2, (a.n + 255) / 256 + 1);
+  copy_out_kernel<<<grid, 256, 0, st>>>(a.stage, a.n, a.chunk_off, a.P, a.dst_cur, a.part_end, a.out);
   return cudaGetLastError();
 }
 
