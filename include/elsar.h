@@ -302,6 +302,22 @@ elsar_status elsar_sort_noalloc(const void* d_in, void* d_out, uint64_t n, const
                                 elsar_stream_t stream);
 
 /* Static description of a status code. */
+/*
+ * Failure-detection self-test of the bounded waits that guard every TMA
+ * pipeline: one CTA waits on an mbarrier phase that nothing completes while
+ * one of its own 4096-byte bulk copies (from d_src, 16-byte aligned, device)
+ * is in flight.  After limit_cycles (1 .. 4e9 SM clock cycles) the wait gives
+ * up, the CTA raises the status word (d_word, 3 x uint32 of device memory),
+ * waits (bounded) for its own copy and returns.  h_result receives the
+ * 3 words: [0] bit 0 = the wait timed out, bit 1 = the in-flight copy was
+ * drained; [1] the byte sum of the copied block; [2] the cycles waited
+ * (saturated).  Returns ELSAR_ETIMEOUT when the wait gave up (the expected
+ * outcome), ELSAR_EINVAL on bad arguments, ELSAR_ECUDA on a CUDA error.
+ * Synchronises the stream.  The context stays usable afterwards.
+ */
+elsar_status elsar_selftest_bounded_wait(const void* d_src, void* d_word, uint64_t limit_cycles,
+                                         elsar_stream_t stream, uint32_t* h_result);
+
 const char* elsar_status_str(elsar_status s);
 
 /* Message of the last failing call on this thread ("" if none). */

@@ -96,6 +96,7 @@ def lib():
             "elsar_sort_host": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
             "elsar_sort_noalloc": (ctypes.c_int, [P, P, U64, PP, P]),
             "elsar_ooc_min_workspace": (SZ, [U64, PP]),
+            "elsar_selftest_bounded_wait": (ctypes.c_int, [P, P, U64, P, ctypes.POINTER(ctypes.c_uint32 * 3)]),
             "elsar_sort_ooc": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_OocStats)]),
             "elsar_mlp_grad_workspace": (SZ, [U64]),
             "elsar_mlp_eval": (ctypes.c_int, [P, P, P, U64, P, P]),
@@ -230,6 +231,15 @@ def sort_ooc(h_in, h_out, n: int, p: Params | None = None, ws=None, budget: int 
     return dict(phase_ms=list(st.phase_ms), h2d_bytes=st.h2d_bytes, d2h_bytes=st.d2h_bytes, chunks=st.chunks,
                 groups=st.groups, chunk_records=st.chunk_records, group_records=st.group_records,
                 model_used=st.model_used, fallback_reason=st.fallback_reason, max_partition=st.max_partition)
+
+
+def selftest_bounded_wait(d_src, d_word, limit_cycles: int, stream=None):
+    """Run the bounded-wait self-test; returns (status, [flags, byte_sum, cycles_waited]).
+    ELSAR_ETIMEOUT (4) is the expected status: the wait gave up as designed."""
+    res = (ctypes.c_uint32 * 3)()
+    rc = lib().elsar_selftest_bounded_wait(_ptr(d_src), _ptr(d_word), limit_cycles, _stream(stream),
+                                           ctypes.byref(res))
+    return rc, list(res)
 
 
 def mlp_eval(d_w, d_knots, d_x, n: int, d_F, stream=None):

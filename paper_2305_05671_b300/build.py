@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libelsar.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["fit.cu", "partition.cu", "sort.cu", "mlp.cu", "batch.cu", "ooc.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["fit.cu", "partition.cu", "sort.cu", "mlp.cu", "batch.cu", "ooc.cu", "selftest.cu", "api.cu", "noalloc.cu"]
 # the model fit must round exactly as written: no contraction into FMA
 EXTRA = {"fit.cu": ["-fmad=false"]}
 

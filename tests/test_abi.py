@@ -68,3 +68,23 @@ def test_status_strings():
 def test_binding_raises():
     with pytest.raises(elsar.ElsarError):
         elsar._check(2)
+
+
+def test_selftest_arguments_rejected_on_host():
+    L = elsar.lib()
+    res = (ctypes.c_uint32 * 3)()
+    # limit out of range, unaligned source, null pointers: EINVAL before any CUDA call
+    assert L.elsar_selftest_bounded_wait(FAKE_WS, FAKE_WS, 0, None, ctypes.byref(res)) == 1
+    assert L.elsar_selftest_bounded_wait(FAKE_WS, FAKE_WS, 5_000_000_000, None, ctypes.byref(res)) == 1
+    assert L.elsar_selftest_bounded_wait(FAKE_WS + 4, FAKE_WS, 1000, None, ctypes.byref(res)) == 1
+    assert L.elsar_selftest_bounded_wait(None, FAKE_WS, 1000, None, ctypes.byref(res)) == 1
+    assert L.elsar_selftest_bounded_wait(FAKE_WS, FAKE_WS, 1000, None, None) == 1
+
+
+def test_ooc_arguments_rejected_on_host():
+    L = elsar.lib()
+    p = elsar.Params().c()
+    assert L.elsar_sort_ooc(FAKE_WS, FAKE_WS, 1 << 32, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 5
+    assert L.elsar_sort_ooc(FAKE_WS, FAKE_WS, 1000, ctypes.byref(p), FAKE_WS + 8, 1 << 40, None, None) == 1
+    assert L.elsar_sort_ooc(None, None, 0, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 0
+    assert elsar.ooc_min_workspace(10**9) > elsar.ooc_min_workspace(10**3) > 64 << 20
