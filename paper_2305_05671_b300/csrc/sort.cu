@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr uint32_t kShortRun = 16;  // runs up to this length get the insertion-sort touch-up
+constexpr uint32_t kRankMax = 128;  // buckets up to this length are ranked inside the digit pass (the touch-up)
 
 struct Misc {
   uint64_t red[2][kWarps];
@@ -39,8 +39,8 @@ struct Tile {
   uint32_t* cnt;   // cap digit counters
   uint16_t* perm;  // cap: sorted order being built
   uint16_t* perm2; // cap: scatter target
-  uint32_t* longs; // cap/16 + 1 long runs of the first digit pass
-  uint32_t* stk;   // kWarps x (cap/16 + 1) refinement stacks
+  uint32_t* longs; // cap/kRankMax + 1 long runs of the first digit pass
+  uint32_t* stk;   // kWarps x (cap/kRankMax + 1) refinement stacks
   uint32_t stk_cap;
   Misc* ms;
 };
@@ -125,18 +125,28 @@ __device__ void block_minmax(const Tile& t, uint32_t m, int sel) {
   __syncthreads();
 }
 
-// insertion sort of perm[s, e) by the full key (the paper's touch-up)
-__device__ __forceinline__ void insertion_sort(const Tile& t, uint32_t s, uint32_t e) {
-  for (uint32_t i = s + 1; i < e; ++i) {
-    const uint16_t v = t.perm[i];
-    const Pair pv = t.A[v];
-    uint32_t k = i;
-    while (k > s && pair_less(pv, t.A[t.perm[k - 1]])) {
-      t.perm[k] = t.perm[k - 1];
-      --k;
+// After a digit pass: position pos of perm holds record j of the bucket
+// [rs, re).  A bucket of 2..kRankMax elements is finished here: every element
+// is placed at its rank by the full key among the bucket (the touch-up: a
+// comparison sort of what the model and the digit left unordered, each
+// element ranked by its own thread, so long buckets of skewed keys spread over
+// all threads); other elements keep their place.  The order is total (the
+// record index breaks ties), so ranks are distinct.
+__device__ __forceinline__ void place_ranked(const Tile& t, uint32_t pos, uint32_t rs, uint32_t re) {
+  const uint16_t j = t.perm[pos];
+  uint32_t dst = pos;
+  if (re - rs >= 2 && re - rs <= kRankMax) {
+    const Pair pj = t.A[j];
+    uint32_t c = 0, q = rs;
+    for (; q + 4 <= re; q += 4) {
+      const uint16_t a0 = t.perm[q], a1 = t.perm[q + 1], a2 = t.perm[q + 2], a3 = t.perm[q + 3];
+      c += (pair_less(t.A[a0], pj) ? 1u : 0u) + (pair_less(t.A[a1], pj) ? 1u : 0u) +
+           (pair_less(t.A[a2], pj) ? 1u : 0u) + (pair_less(t.A[a3], pj) ? 1u : 0u);
     }
-    t.perm[k] = v;
+    for (; q < re; ++q) c += pair_less(t.A[t.perm[q]], pj) ? 1u : 0u;
+    dst = rs + c;
   }
+  t.perm2[dst] = j;
 }
 
 __device__ __forceinline__ uint64_t warp_min(uint64_t v) {
@@ -148,10 +158,11 @@ __device__ __forceinline__ uint64_t warp_max(uint64_t v) {
   return v;
 }
 
-// One warp sorts perm[s0, s0+len0) completely: counting-sort refinement on a
-// digit of the run's own key range, recursively (explicit stack), with
-// insertion sort for short sub-runs.  Every pass splits a run into at least
-// two non-empty parts, so it terminates.
+// One warp sorts perm[s0, s0+len0) (len0 > kRankMax) completely: a counting
+// pass on a digit of the run's own key range, its buckets of up to kRankMax
+// ranked in place and longer ones refined the same way (explicit stack).
+// Every pass splits a run into at least two non-empty parts, so it
+// terminates.
 __device__ void warp_refine(const Tile& t, uint32_t s0, uint32_t len0) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t* stk = t.stk + warp * t.stk_cap;
@@ -185,7 +196,7 @@ __device__ void warp_refine(const Tile& t, uint32_t s0, uint32_t len0) {
       if (mn < mx || sel == 2) break;
       ++sel;
     }
-    const uint32_t logD = 31 - __clz(len);  // len > kShortRun, so D >= 16
+    const uint32_t logD = 31 - __clz(len);  // len > kRankMax, so D >= 128
     const uint32_t D = 1u << logD;
     const uint64_t span = mx - mn;
     const uint32_t bits = 64 - __clzll((long long)span);
@@ -221,19 +232,27 @@ __device__ void warp_refine(const Tile& t, uint32_t s0, uint32_t len0) {
     __syncwarp();
     for (uint32_t i = lane; i < len; i += 32) t.perm[s + i] = t.perm2[s + i];
     __syncwarp();
+    // buckets up to kRankMax ranked in place; longer ones go on the stack
+    for (uint32_t i = lane; i < len; i += 32) {
+      const uint32_t d = (uint32_t)((sel_key(t, t.perm[s + i], sel) - mn) >> shift);
+      place_ranked(t, s + i, d ? t.cnt[s + d - 1] : s, t.cnt[s + d]);
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < len; i += 32) t.perm[s + i] = t.perm2[s + i];
+    __syncwarp();
     for (uint32_t d = lane; d < D; d += 32) {
       const uint32_t ss = d ? t.cnt[s + d - 1] : s, ee = t.cnt[s + d];
       const uint32_t l = ee - ss;
-      if (l >= 2 && l <= kShortRun) insertion_sort(t, ss, ee);
-      else if (l > kShortRun) stk[atomicAdd(top, 1u)] = (ss << 16) | l;
+      if (l > kRankMax) stk[atomicAdd(top, 1u)] = (ss << 16) | l;
     }
     __syncwarp();
   }
 }
 
 // Sort the tile A[0, m) (m <= cap; E filled): on return perm[0, m) lists A in
-// (hi, lo) order.  First digit pass block-wide over the whole tile, then the
-// long runs are refined by warps in parallel.
+// (hi, lo) order.  First digit pass block-wide over the whole tile, its short
+// buckets ranked in place by all threads, then the long runs are finished by
+// warps in parallel.
 __device__ void tile_sort(const Tile& t, uint32_t m) {
   Misc& ms = *t.ms;
   if (m <= 1) {
@@ -284,11 +303,17 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
     t.perm[pos] = (uint16_t)j;
   }
   __syncthreads();
+  // buckets up to kRankMax ranked in place (every element by its own thread)
+  for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
+    const uint32_t d = (uint32_t)((sel_key(t, t.perm[pos], sel) - kmin) >> shift);
+    place_ranked(t, pos, d ? t.cnt[d - 1] : 0, t.cnt[d]);
+  }
+  __syncthreads();
+  for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) t.perm[pos] = t.perm2[pos];
   for (uint32_t d = threadIdx.x; d < D; d += kThreads) {
     const uint32_t s = d ? t.cnt[d - 1] : 0, e = t.cnt[d];
     const uint32_t len = e - s;
-    if (len >= 2 && len <= kShortRun) insertion_sort(t, s, e);
-    else if (len > kShortRun) t.longs[atomicAdd(&ms.nlong, 1u)] = (s << 16) | len;
+    if (len > kRankMax) t.longs[atomicAdd(&ms.nlong, 1u)] = (s << 16) | len;
   }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31;
@@ -472,7 +497,7 @@ __device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
   p += (size_t)cap * 2;
   t.perm2 = reinterpret_cast<uint16_t*>(p);
   p += (size_t)cap * 2;
-  t.stk_cap = cap / 16 + 1;
+  t.stk_cap = cap / kRankMax + 1;  // disjoint runs longer than kRankMax
   t.longs = reinterpret_cast<uint32_t*>(p);
   p += (size_t)t.stk_cap * 4;
   t.stk = reinterpret_cast<uint32_t*>(p);
@@ -521,7 +546,7 @@ __global__ void part_items_kernel(const uint32_t* cuts, const uint32_t* item_of_
 }  // namespace
 
 size_t sort_smem_bytes(uint32_t cap) {
-  const size_t stk = (size_t)(cap / 16 + 1) * 4;
+  const size_t stk = (size_t)(cap / kRankMax + 1) * 4;
   return (size_t)cap * (sizeof(Pair) + 8 + 4 + 2 + 2) + stk * (1 + kWarps) + 16 + sizeof(Misc);
 }
 
