@@ -92,7 +92,7 @@ elsar_status resolve(uint64_t n, const elsar_params* p, Resolved* r) {
 
 struct Layout {
   size_t ctrl, model, pairsA, pairsB, bin_off, part_off, cuts, cursor, items, item_flag, oversize, samp, pnode, sums,
-      fc, sets, mlp_phi, mlp_y, mlp_partial, mlp_m, mlp_v, swap, judge, total;
+      fc, sets, seg, mlp_phi, mlp_y, mlp_partial, mlp_m, mlp_v, swap, judge, total;
 };
 
 constexpr uint64_t kMlpTrainMax = 2000000;  // keys the network trains on (every k-th of the sorted sample)
@@ -128,6 +128,7 @@ Layout layout(uint64_t n, const Resolved& r) {
   L.sums = take(cap * 48);
   L.fc = take(cap * 8);  // split fanouts + child offsets of one level
   L.sets = take(sizeof(SetInfo));
+  L.seg = take(coarse_segments(n) * kMaxCoarse * 4);
   const bool mlp = r.kind == ELSAR_MODEL_MLP;
   const uint64_t nt = mlp ? mlp_ntrain(r.S) : 0;
   L.mlp_phi = take(nt * 12 * 4);
@@ -304,6 +305,8 @@ PartArgs part_args(const void* d_model, const void* d_records, uint64_t n, const
   a.item_flag = at<uint32_t>(d_ws, L.item_flag);
   a.oversize = at<uint32_t>(d_ws, L.oversize);
   a.ctrl = at<uint32_t>(d_ws, L.ctrl);
+  a.seg_hist = at<uint32_t>(d_ws, L.seg);
+  a.mid = at<void>(d_ws, L.pairsB);
   a.stream = st;
   a.launches = launches;
   return a;
@@ -474,6 +477,9 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
     if (ev[1]) cudaEventRecord(ev[1], st);
     PartArgs a = part_args(model, d_in, n, r, at<void>(d_ws, L.pairsB), at<uint32_t>(d_ws, L.bin_off),
                            at<uint64_t>(d_ws, L.part_off), d_ws, L, st, &launches);
+    // between the scatter passes the pairs wait in the output record buffer
+    // (n x 100 bytes, written only by the final gather), 16-byte aligned
+    a.mid = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(d_out) + 15) & ~(uintptr_t)15);
     a.ev[0] = ev[2];
     a.ev[1] = ev[3];
     a.ev[2] = ev[4];
@@ -702,6 +708,7 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
   sa.dst_next = dst_next;
   sa.part_end = a.part_off + 1;
   sa.out = dv_out;
+  sa.ctrl = a.ctrl;
   auto issue_in = [&](uint64_t c) {
     const int b = (int)(c & 1);
     const uint64_t cn = std::min<uint64_t>(C, n - c * C);
@@ -772,6 +779,7 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
         s = cuda_fail(e, "out-of-core cuts");
         break;
       }
+      if ((s = device_status(d_ws, Lf, st)) != ELSAR_OK) break;  // a classify wait gave up
       uint64_t mx = 0;
       for (uint32_t q = 0; q < r.P; ++q) mx = std::max<uint64_t>(mx, part_off[q + 1] - part_off[q]);
       if (fr.kind == ELSAR_MODEL_MLP && (double)mx * r.P > 1.1 * (double)n) {

@@ -236,10 +236,22 @@ struct PartArgs {
   uint32_t* item_flag;   // B   scratch (becomes the item id of every bin)
   uint32_t* oversize;    // B   item ids of oversize items
   uint32_t* ctrl;        // control words
+  void* mid;             // n pairs (scratch, 16-byte aligned): coarse-bin order between the two scatter passes
+  uint32_t* seg_hist;    // coarse_segments(n) x kMaxCoarse counts of every classify CTA
   cudaStream_t stream;
   uint32_t* launches;
   cudaEvent_t ev[4];  // optional: after classify, after scan/cuts/items, after scatter
 };
+
+// Two-pass scatter: coarse bins of 2^coarse_shift(log2B) fine bins, at most
+// kMaxCoarse of them; classify CTAs (at most kMaxSegments) count per coarse bin.
+constexpr uint32_t kMaxCoarse = 512;
+constexpr uint32_t kMaxSegments = 2048;
+inline uint32_t coarse_shift(uint32_t log2B) { return log2B > 9 ? log2B - 9 : 0; }
+inline uint64_t coarse_segments(uint64_t n) {
+  const uint64_t t = (n + 255) / 256 + 1;
+  return t < kMaxSegments ? t : kMaxSegments;
+}
 
 cudaError_t partition_records(const PartArgs& a);
 cudaError_t build_items(const PartArgs& a);
@@ -309,6 +321,7 @@ struct OocSplitArgs {
   uint64_t* dst_cur;         // P: this chunk's destination of every partition
   const uint64_t* part_end;  // P: end of every partition's output range (records)
   uint8_t* out;              // the output records (host memory mapped into the device)
+  const uint32_t* ctrl;      // control words (status word: classify gave up)
 };
 // stable split of a chunk by partition into `stage`
 cudaError_t ooc_split_chunk(const OocSplitArgs& a, cudaStream_t st);

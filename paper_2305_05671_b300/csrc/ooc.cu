@@ -31,8 +31,10 @@ __global__ void bin_to_part_kernel(const uint32_t* __restrict__ cuts, uint32_t P
 __global__ void __launch_bounds__(kTileThreads) tile_split_kernel(const Pair* __restrict__ pairs, uint64_t n,
                                                                   const uint16_t* __restrict__ lut, uint32_t P,
                                                                   uint32_t* __restrict__ tile_hist,
-                                                                  uint16_t* __restrict__ rank) {
+                                                                  uint16_t* __restrict__ rank,
+                                                                  const uint32_t* ctrl) {
   __shared__ uint32_t key[kTile];
+  if (ctrl[kStatusWord]) return;  // classify gave up: its fine bins are not valid
   const uint64_t t0 = (uint64_t)blockIdx.x * kTile;
   const uint32_t m = (uint32_t)min((uint64_t)kTile, n - t0);
   for (uint32_t i = threadIdx.x; i < kTile; i += kTileThreads)
@@ -133,7 +135,8 @@ __global__ void __launch_bounds__(1024) part_scan_kernel(const uint32_t* __restr
 __global__ void split_records_kernel(const uint8_t* __restrict__ in, uint64_t n, const Pair* __restrict__ pairs,
                                      const uint16_t* __restrict__ lut, const uint32_t* __restrict__ tile_hist,
                                      const uint32_t* __restrict__ part_off, const uint16_t* __restrict__ rank,
-                                     uint32_t P, uint8_t* __restrict__ out) {
+                                     uint32_t P, uint8_t* __restrict__ out, const uint32_t* ctrl) {
+  if (ctrl[kStatusWord]) return;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warps = (uint64_t)gridDim.x * (blockDim.x >> 5);
   const uint32_t* in32 = reinterpret_cast<const uint32_t*>(in);
@@ -211,12 +214,12 @@ cudaError_t ooc_bin_to_part(const uint32_t* cuts, uint32_t P, uint32_t B, uint16
 cudaError_t ooc_split_chunk(const OocSplitArgs& a, cudaStream_t st) {
   if (!a.n) return cudaSuccess;
   const uint64_t tiles = ooc_tiles(a.n);
-  tile_split_kernel<<<(unsigned)tiles, kTileThreads, 0, st>>>(a.pairs, a.n, a.lut, a.P, a.tile_hist, a.rank);
+  tile_split_kernel<<<(unsigned)tiles, kTileThreads, 0, st>>>(a.pairs, a.n, a.lut, a.P, a.tile_hist, a.rank, a.ctrl);
   column_scan_kernel<<<(a.P + 255) / 256, 256, 0, st>>>(a.tile_hist, (uint32_t)tiles, a.P, a.part_count);
   part_scan_kernel<<<1, 1024, 0, st>>>(a.part_count, a.P, a.chunk_off, a.dst_next, a.dst_cur);
   const unsigned grid = (unsigned)min((uint64_t)sm_count() * 16, (a.n + 255) / 256 + 1);
   split_records_kernel<<<grid, 256, 0, st>>>(a.chunk, a.n, a.pairs, a.lut, a.tile_hist, a.chunk_off, a.rank, a.P,
-                                             a.stage);
+                                             a.stage, a.ctrl);
   return cudaGetLastError();
 }
 

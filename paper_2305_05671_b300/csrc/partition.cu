@@ -1,6 +1,8 @@
 // Model-based partitioning (Sec. 3.3, Algorithm 1 reader loop, Eq. 1) on the
 // GPU: pack + classify + histogram, scan of the fine bins, partition cuts,
-// scatter of 16-byte pairs into bin order, and the work items of the sort.
+// scatter of 16-byte pairs into bin order (two passes with their cursors in
+// shared memory: coarse bins, then the fine bins inside each), and the work
+// items of the sort.
 #include "common.cuh"
 
 namespace elsar {
@@ -12,17 +14,17 @@ inline uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
 constexpr int kThreads = 256;
 constexpr int kUnroll = 8;
 constexpr int kTileRecs = kThreads;  // records staged per bulk copy (25,600 bytes)
-constexpr int kStages = 2;
 constexpr uint32_t kTileBytes = kTileRecs * kRecord;
 
-__device__ __forceinline__ void classify_one(const Pair& key, uint64_t i, const uint64_t* __restrict__ t,
-                                             const uint32_t* __restrict__ lut, Pair* __restrict__ pairs,
-                                             uint32_t* __restrict__ hist) {
+__device__ __forceinline__ uint32_t classify_one(const Pair& key, uint64_t i, const uint64_t* __restrict__ t,
+                                                 const uint32_t* __restrict__ lut, Pair* __restrict__ pairs,
+                                                 uint32_t* __restrict__ hist) {
   Pair p = key;
   const uint32_t q = splitter_search(t, lut, enc9_pair(p));
   p.lo |= q;
   pairs[i] = p;
   atomicAdd(hist + q, 1u);
+  return q;
 }
 
 __device__ __forceinline__ Pair pair_from_words(uint32_t a, uint32_t b, uint32_t c) {
@@ -33,28 +35,37 @@ __device__ __forceinline__ Pair pair_from_words(uint32_t a, uint32_t b, uint32_t
 }
 
 // Pass A, TMA form: tiles of 256 records (25,600 bytes, 16-byte aligned when
-// the record buffer is) are bulk-copied into shared memory, double buffered
-// on mbarriers; each thread packs one key from shared memory, classifies it
-// and counts it.  The input-order pair carries {hi, (key bytes 8-9) << 32 | q}.
+// the record buffer is) are bulk-copied into shared memory, NS tiles in
+// flight on their own mbarriers.  A round takes the CTA's next NS tiles:
+// every thread copies the key words of its KPT = NS*256/NT records out of the
+// stages, the stages are refilled with the following round's tiles at once,
+// and the thread then packs, classifies and counts its keys -- the splitter
+// searches run in lockstep, so their loads overlap one another and the
+// refill.  The input-order pair carries {hi, (key bytes 8-9) << 32 | q}.
 // Every wait is bounded: on timeout the CTA raises the status word, waits
 // (bounded) for its own copies in flight and leaves.
-__global__ void __launch_bounds__(kThreads) classify_tma_kernel(const uint8_t* __restrict__ rec, uint64_t n,
-                                                                const uint64_t* __restrict__ t,
-                                                                const uint32_t* __restrict__ lut,
-                                                                Pair* __restrict__ pairs, uint32_t* __restrict__ hist,
-                                                                uint32_t* ctrl) {
-  extern __shared__ __align__(128) uint8_t buf[];  // kStages x kTileBytes
-  __shared__ uint64_t bar[kStages];
+template <int NT, int NS>
+__global__ void __launch_bounds__(NT) classify_tma_kernel(const uint8_t* __restrict__ rec, uint64_t n,
+                                                          const uint64_t* __restrict__ t,
+                                                          const uint32_t* __restrict__ lut, Pair* __restrict__ pairs,
+                                                          uint32_t* __restrict__ hist, uint32_t* ctrl, uint32_t cshift,
+                                                          uint32_t* __restrict__ seg_hist, uint32_t seg_stride) {
+  constexpr int KPT = NS * kTileRecs / NT;
+  extern __shared__ __align__(128) uint8_t buf[];  // NS x kTileBytes
+  __shared__ uint64_t bar[NS];
+  __shared__ uint32_t hc[kMaxCoarse];  // this CTA's counts per coarse bin
   const uint64_t ntiles = n / kTileRecs;
+  const uint64_t G = gridDim.x;
+  for (uint32_t c = threadIdx.x; c < kMaxCoarse; c += NT) hc[c] = 0;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < NS; ++s) mbar_init(&bar[s], 1);
     fence_mbar_init();
   }
   __syncthreads();
-  uint32_t issued[kStages] = {};  // copies issued per stage (thread 0)
+  uint32_t issued[NS] = {};  // copies issued per stage (thread 0)
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
-      const uint64_t k = blockIdx.x + (uint64_t)s * gridDim.x;
+    for (int s = 0; s < NS; ++s) {
+      const uint64_t k = blockIdx.x + (uint64_t)s * G;
       if (k < ntiles) {
         mbar_expect_tx(&bar[s], kTileBytes);
         bulk_g2s(buf + s * kTileBytes, rec + k * kTileBytes, kTileBytes, &bar[s]);
@@ -63,26 +74,75 @@ __global__ void __launch_bounds__(kThreads) classify_tma_kernel(const uint8_t* _
     }
   }
   bool failed = false;
-  uint32_t j = 0;
-  for (uint64_t k = blockIdx.x; k < ntiles; k += gridDim.x, ++j) {
-    const int s = j % kStages;
-    const uint32_t parity = (j / kStages) & 1;
-    const bool ok = mbar_wait(&bar[s], parity, kWaitLimitCycles);
-    if (__syncthreads_or(!ok)) {
+  uint32_t round = 0;
+  for (uint64_t k0 = blockIdx.x; k0 < ntiles; k0 += NS * G, ++round) {
+    uint32_t w[KPT][3];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const int slot = threadIdx.x + j * NT, s = slot / kTileRecs, r = slot % kTileRecs;
+      w[j][0] = w[j][1] = w[j][2] = 0x20202020u;  // a key of spaces where the round has no tile
+      if (k0 + s * G < ntiles) {
+        ok = ok && mbar_wait(&bar[s], round & 1, kWaitLimitCycles);
+        const uint32_t* ws = reinterpret_cast<const uint32_t*>(buf + s * kTileBytes + r * kRecord);
+        w[j][0] = ws[0];
+        w[j][1] = ws[1];
+        w[j][2] = ws[2];
+      }
+    }
+    if (__syncthreads_or(!ok)) {  // every thread is also done reading the stages
       failed = true;
       break;
     }
-    const uint32_t* w = reinterpret_cast<const uint32_t*>(buf + s * kTileBytes + threadIdx.x * kRecord);
-    const uint64_t i = k * kTileRecs + threadIdx.x;
-    classify_one(pair_from_words(w[0], w[1], w[2]), i, t, lut, pairs, hist);
-    __syncthreads();  // every thread is done with this stage
     if (threadIdx.x == 0) {
-      const uint64_t k2 = k + (uint64_t)kStages * gridDim.x;
-      if (k2 < ntiles) {
-        fence_proxy_async();
-        mbar_expect_tx(&bar[s], kTileBytes);
-        bulk_g2s(buf + s * kTileBytes, rec + k2 * kTileBytes, kTileBytes, &bar[s]);
-        ++issued[s];
+      fence_proxy_async();
+#pragma unroll
+      for (int s = 0; s < NS; ++s) {
+        const uint64_t k2 = k0 + (uint64_t)(s + NS) * G;
+        if (k2 < ntiles) {
+          mbar_expect_tx(&bar[s], kTileBytes);
+          bulk_g2s(buf + s * kTileBytes, rec + k2 * kTileBytes, kTileBytes, &bar[s]);
+          ++issued[s];
+        }
+      }
+    }
+    Pair pr[KPT];
+    uint64_t x[KPT];
+    uint32_t lo[KPT], hi[KPT];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const int slot = threadIdx.x + j * NT, s = slot / kTileRecs;
+      pr[j] = pair_from_words(w[j][0], w[j][1], w[j][2]);
+      x[j] = enc9_pair(pr[j]);
+      const uint32_t c = (uint32_t)(x[j] >> kFineLutShift);
+      const bool v = k0 + s * G < ntiles;
+      lo[j] = v ? __ldg(lut + c) : 0;
+      hi[j] = v ? __ldg(lut + c + 1) : 0;
+    }
+    for (;;) {
+      bool more = false;
+#pragma unroll
+      for (int j = 0; j < KPT; ++j) {
+        if (lo[j] < hi[j]) {
+          const uint32_t mid = (lo[j] + hi[j] + 1) >> 1;
+          if (__ldg(t + mid) <= x[j]) lo[j] = mid;
+          else hi[j] = mid - 1;
+          more = true;
+        }
+      }
+      if (!more) break;
+    }
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const int slot = threadIdx.x + j * NT, s = slot / kTileRecs, r = slot % kTileRecs;
+      const uint64_t k = k0 + s * G;
+      if (k < ntiles) {
+        const uint32_t q = lo[j];
+        Pair p = pr[j];
+        p.lo |= q;
+        pairs[k * kTileRecs + r] = p;
+        atomicAdd(hist + q, 1u);
+        if (seg_hist) atomicAdd(&hc[q >> cshift], 1u);
       }
     }
   }
@@ -90,24 +150,45 @@ __global__ void __launch_bounds__(kThreads) classify_tma_kernel(const uint8_t* _
     if (threadIdx.x == 0) {
       atomicOr(ctrl + kStatusWord, 1u);
       // copies still in flight target this CTA's shared memory: wait for them, bounded
-      for (int s = 0; s < kStages; ++s) {
-        // stage s completed (j_s) phases so far; its last issued copy ends phase issued[s]-1
+      for (int s = 0; s < NS; ++s) {
+        // the last copy issued on stage s completes that stage's phase issued[s]-1
         if (issued[s]) mbar_wait(&bar[s], (issued[s] - 1) & 1, kWaitLimitCycles);
       }
     }
     return;
   }
-  // ragged tail (n mod 256 records): plain loads
-  for (uint64_t i = ntiles * kTileRecs + blockIdx.x * (uint64_t)kThreads + threadIdx.x; i < n;
-       i += (uint64_t)gridDim.x * kThreads)
-    classify_one(load_pair(rec + i * kRecord, 0), i, t, lut, pairs, hist);
+  // ragged tail (n mod 256 records, so CTA 0 alone): plain loads
+  for (uint64_t i = ntiles * kTileRecs + blockIdx.x * (uint64_t)NT + threadIdx.x; i < n && blockIdx.x == 0;
+       i += (uint64_t)NT) {
+    const uint32_t q = classify_one(load_pair(rec + i * kRecord, 0), i, t, lut, pairs, hist);
+    if (seg_hist) atomicAdd(&hc[q >> cshift], 1u);
+  }
+  if (seg_hist) {
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < kMaxCoarse; c += NT) seg_hist[c * seg_stride + blockIdx.x] = hc[c];
+  }
 }
+
+#ifndef ELSAR_CLASSIFY_NT
+#define ELSAR_CLASSIFY_NT 256
+#endif
+#ifndef ELSAR_CLASSIFY_NS
+#define ELSAR_CLASSIFY_NS 2
+#endif
+constexpr int kClassifyThreads = ELSAR_CLASSIFY_NT;
+constexpr int kClassifyStages = ELSAR_CLASSIFY_NS;
+#define CLASSIFY_TMA classify_tma_kernel<kClassifyThreads, kClassifyStages>
 
 // Pass A, plain form (record buffers that are not 16-byte aligned).
 __global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __restrict__ rec, uint64_t n,
                                                             const uint64_t* __restrict__ t,
                                                             const uint32_t* __restrict__ lut,
-                                                            Pair* __restrict__ pairs, uint32_t* __restrict__ hist) {
+                                                            Pair* __restrict__ pairs, uint32_t* __restrict__ hist,
+                                                            uint32_t cshift, uint32_t* __restrict__ seg_hist,
+                                                            uint32_t seg_stride) {
+  __shared__ uint32_t hc[kMaxCoarse];
+  for (uint32_t c = threadIdx.x; c < kMaxCoarse; c += kThreads) hc[c] = 0;
+  __syncthreads();
   const uint64_t stride = (uint64_t)gridDim.x * kThreads * kUnroll;
   for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads * kUnroll + threadIdx.x; i0 < n; i0 += stride) {
     Pair p[kUnroll];
@@ -119,8 +200,15 @@ __global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __res
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint64_t i = i0 + (uint64_t)u * kThreads;
-      if (i < n) classify_one(p[u], i, t, lut, pairs, hist);
+      if (i < n) {
+        const uint32_t q = classify_one(p[u], i, t, lut, pairs, hist);
+        if (seg_hist) atomicAdd(&hc[q >> cshift], 1u);
+      }
     }
+  }
+  if (seg_hist) {
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < kMaxCoarse; c += kThreads) seg_hist[c * seg_stride + blockIdx.x] = hc[c];
   }
 }
 
@@ -161,6 +249,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_bins(const uint32_t* hist, 
                                                           uint32_t* ctrl) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t carry_sh;
+  if (ctrl[kStatusWord]) return;  // classify gave up: nothing downstream runs
   if (threadIdx.x == 0) carry_sh = 0;
   uint32_t mx = 0;
   __syncthreads();
@@ -239,6 +328,7 @@ __global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __r
                                                              uint32_t* oversize, uint32_t* ctrl) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t carry_sh;
+  if (ctrl[kStatusWord]) return;
   const uint32_t W = cap / 2;
   if (threadIdx.x == 0) carry_sh = 0;
   __syncthreads();
@@ -275,34 +365,218 @@ __global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __r
   }
 }
 
-// Pass B: pairs (input order) -> bin order; slot from an atomic cursor per
-// bin; the fine bin rides in the pair, the record index replaces it.
-__global__ void __launch_bounds__(kThreads) scatter_kernel(const Pair* __restrict__ in, uint64_t n,
-                                                           uint32_t* __restrict__ cursor, Pair* __restrict__ out) {
-  const uint64_t stride = (uint64_t)gridDim.x * kThreads * kUnroll;
-  for (uint64_t i0 = (uint64_t)blockIdx.x * kThreads * kUnroll + threadIdx.x; i0 < n; i0 += stride) {
-    Pair p[kUnroll];
-    uint32_t slot[kUnroll];
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint64_t i = i0 + (uint64_t)u * kThreads;
-      if (i < n) p[u] = in[i];
+// Coarse offsets: seg[c][b] (counts of classify CTA b in coarse bin c) becomes
+// the start of CTA b's slots in coarse bin c: the coarse bin's start
+// bin_off[c << cshift] plus the counts of the CTAs before b.  A warp per c.
+__global__ void coarse_offsets_kernel(uint32_t* __restrict__ seg, uint32_t seg_stride, uint32_t G, uint32_t C,
+                                      uint32_t cshift, const uint32_t* __restrict__ bin_off, const uint32_t* ctrl) {
+  if (ctrl[kStatusWord]) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (c >= C) return;
+  uint32_t* col = seg + (size_t)c * seg_stride;
+  uint32_t carry = bin_off[c << cshift];
+  for (uint32_t b0 = 0; b0 < G; b0 += 32) {
+    const uint32_t b = b0 + lane;
+    const uint32_t h = b < G ? col[b] : 0;
+    uint32_t incl = h;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= (uint32_t)d) incl += y;
     }
-#pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint64_t i = i0 + (uint64_t)u * kThreads;
-      if (i < n) slot[u] = atomicAdd(cursor + (uint32_t)p[u].lo, 1u);
+    if (b < G) col[b] = carry + incl - h;
+    carry += __shfl_sync(0xffffffffu, incl, 31);
+  }
+}
+
+// Scatter through shared memory: the pairs a CTA holds (PER per thread) are
+// first put in bin order in shared memory (rank inside the batch from a
+// shared counter, offsets from a block scan), then written out slot by slot,
+// so the pairs of one bin leave as one contiguous run (whole lines rather
+// than 16-byte pieces scattered over the device).  cur[] holds every bin's
+// next output slot and advances by the batch's counts.
+__device__ __forceinline__ void prefetch_l2_line(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+constexpr int kStageThreads = 512;
+constexpr int kStagePer = 8;
+constexpr uint32_t kStagePairs = kStageThreads * kStagePer;  // 4096 pairs = 64 KB
+
+struct Stage {
+  Pair* pairs;      // kStagePairs
+  uint16_t* binof;  // kStagePairs
+  uint32_t* cnt;    // nb: counts of the batch
+  uint32_t* off;    // nb: exclusive offsets in the batch
+  uint32_t* cur;    // nb: next output slot
+  uint32_t* wsum;   // 33
+};
+
+__device__ __forceinline__ uint32_t stage_scan(uint32_t v, uint32_t* wsum) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t incl = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = lane < kStageThreads / 32 ? wsum[lane] : 0;
+    uint32_t wi = w;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= (uint32_t)d) wi += y;
     }
+    if (lane < kStageThreads / 32) wsum[lane] = wi - w;
+  }
+  __syncthreads();
+  const uint32_t r = wsum[warp] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+// one batch: p[k] valid when bin[k] < nb; out slots checked against `bound`
+__device__ void stage_scatter(const Stage& S, uint32_t nb, const Pair (&p)[kStagePer], const uint32_t (&bin)[kStagePer],
+                              Pair* __restrict__ out, uint64_t bound) {
+  uint32_t r[kStagePer];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) {
-      const uint64_t i = i0 + (uint64_t)u * kThreads;
+  for (int k = 0; k < kStagePer; ++k)
+    if (bin[k] < nb) r[k] = atomicAdd(&S.cnt[bin[k]], 1u);
+  __syncthreads();
+  // exclusive offsets of the nb counts: each thread scans a contiguous group
+  const uint32_t per = (nb + kStageThreads - 1) / kStageThreads;
+  const uint32_t g0 = min(nb, threadIdx.x * per), g1 = min(nb, g0 + per);
+  uint32_t local = 0;
+  for (uint32_t c = g0; c < g1; ++c) local += S.cnt[c];
+  uint32_t run = stage_scan(local, S.wsum);
+  for (uint32_t c = g0; c < g1; ++c) {
+    S.off[c] = run;
+    run += S.cnt[c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kStagePer; ++k)
+    if (bin[k] < nb) {
+      const uint32_t sl = S.off[bin[k]] + r[k];
+      S.pairs[sl] = p[k];
+      S.binof[sl] = (uint16_t)bin[k];
+    }
+  __syncthreads();
+  const uint32_t total = S.off[nb - 1] + S.cnt[nb - 1];
+  for (uint32_t sl = threadIdx.x; sl < total; sl += kStageThreads) {
+    const uint32_t c = S.binof[sl];
+    const uint64_t dst = (uint64_t)S.cur[c] + (sl - S.off[c]);
+    if (dst < bound) out[dst] = S.pairs[sl];
+  }
+  __syncthreads();
+  for (uint32_t c = threadIdx.x; c < nb; c += kStageThreads) {
+    S.cur[c] += S.cnt[c];
+    S.cnt[c] = 0;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ Stage carve_stage(uint8_t* smem, uint32_t nb) {
+  Stage S;
+  S.pairs = reinterpret_cast<Pair*>(smem);
+  S.binof = reinterpret_cast<uint16_t*>(smem + kStagePairs * sizeof(Pair));
+  uint32_t* w = reinterpret_cast<uint32_t*>(smem + kStagePairs * (sizeof(Pair) + 2));
+  S.cnt = w;
+  S.off = w + nb;
+  S.cur = w + 2 * nb;
+  S.wsum = w + 3 * nb;
+  return S;
+}
+
+size_t stage_smem_bytes(uint32_t nb) { return kStagePairs * (sizeof(Pair) + 2) + (3 * (size_t)nb + 33) * 4; }
+
+// Pass B1: pairs (input order) -> coarse-bin order.  CTA b takes the same
+// records as classify's CTA b -- units of U records, unit u to CTA u mod G;
+// the ragged last unit to CTA 0 (TMA classify) or to its own CTA (plain
+// classify) -- so its counts per coarse bin are the ones classify wrote, and
+// its slots in coarse bin c start at seg[c][b].  The record index replaces
+// the fine bin in lo; the fine bin's place inside its coarse bin rides in
+// bits 48.. of lo for pass B2.
+__global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const Pair* __restrict__ in, uint64_t n,
+                                                                       uint32_t U, int tail_to_first,
+                                                                       const uint32_t* __restrict__ seg,
+                                                                       uint32_t seg_stride, uint32_t cshift,
+                                                                       uint32_t C, Pair* __restrict__ out,
+                                                                       const uint32_t* ctrl) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  if (ctrl[kStatusWord]) return;
+  const Stage S = carve_stage(smem, C);
+  for (uint32_t c = threadIdx.x; c < C; c += kStageThreads) {
+    S.cnt[c] = 0;
+    S.cur[c] = seg[(size_t)c * seg_stride + blockIdx.x];
+  }
+  __syncthreads();
+  const uint32_t fmask = (1u << cshift) - 1;
+  const uint64_t G = gridDim.x, b = blockIdx.x;
+  const uint64_t nfull = n / U;
+  const uint64_t mine_full = b < nfull ? (nfull - b + G - 1) / G : 0;
+  const bool tail = (n % U) && b == (tail_to_first ? 0 : nfull % G);
+  const uint64_t mine = mine_full + (tail ? 1 : 0);  // units of this CTA: b, b+G, ..., then the ragged one
+  const uint32_t upb = kStagePairs / U;                // units per batch (U divides kStagePairs)
+  for (uint64_t k0 = 0; k0 < mine; k0 += upb) {
+    {  // the next batch's lines into L2 while this one is staged (one 128-byte line per thread)
+      const uint32_t j = threadIdx.x * 8;
+      const uint64_t ku = k0 + upb + j / U;
+      if (ku < mine_full) prefetch_l2_line(in + (b + ku * G) * U + j % U);
+    }
+    Pair p[kStagePer];
+    uint32_t bin[kStagePer];
+#pragma unroll
+    for (int k = 0; k < kStagePer; ++k) {
+      const uint32_t j = threadIdx.x + k * kStageThreads;  // place in the batch
+      const uint64_t ku = k0 + j / U;
+      const uint64_t unit = ku < mine_full ? b + ku * G : (ku < mine ? nfull : ~0ull);
+      const uint64_t i = unit == ~0ull ? n : unit * U + j % U;
+      bin[k] = ~0u;
       if (i < n) {
-        Pair o;
-        o.hi = p[u].hi;
-        o.lo = (p[u].lo & 0xFFFFFFFF00000000ull) | (uint32_t)i;
-        out[slot[u]] = o;
+        const Pair q = in[i];
+        const uint32_t f = (uint32_t)q.lo;
+        bin[k] = min(f >> cshift, C - 1);
+        p[k].hi = q.hi;
+        p[k].lo = (q.lo & 0x0000FFFF00000000ull) | ((uint64_t)(f & fmask) << 48) | (uint32_t)i;
       }
     }
+    stage_scatter(S, C, p, bin, out, n);
+  }
+}
+
+// Pass B2: one CTA per coarse bin: its pairs to their fine bins (2^cshift of
+// them), through the same shared-memory staging.
+__global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pair* __restrict__ in,
+                                                                     const uint32_t* __restrict__ bin_off, uint32_t B,
+                                                                     uint32_t cshift, Pair* __restrict__ out,
+                                                                     const uint32_t* ctrl) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  if (ctrl[kStatusWord]) return;
+  const uint32_t nf = 1u << cshift;
+  const Stage S = carve_stage(smem, nf);
+  const uint32_t f0 = blockIdx.x << cshift;
+  for (uint32_t f = threadIdx.x; f < nf; f += kStageThreads) {
+    S.cnt[f] = 0;
+    S.cur[f] = bin_off[min(B, f0 + f)];
+  }
+  __syncthreads();
+  const uint32_t s = bin_off[f0], e = bin_off[min(B, f0 + nf)];
+  for (uint32_t i0 = s; i0 < e; i0 += kStagePairs) {
+    if (i0 + kStagePairs + threadIdx.x * 8 < e) prefetch_l2_line(in + i0 + kStagePairs + threadIdx.x * 8);
+    Pair p[kStagePer];
+    uint32_t bin[kStagePer];
+#pragma unroll
+    for (int k = 0; k < kStagePer; ++k) {
+      const uint32_t i = i0 + threadIdx.x + k * kStageThreads;
+      bin[k] = ~0u;
+      if (i < e) {
+        const Pair q = in[i];
+        bin[k] = (uint32_t)(q.lo >> 48) & (nf - 1);
+        p[k].hi = q.hi;
+        p[k].lo = q.lo & 0x0000FFFFFFFFFFFFull;
+      }
+    }
+    stage_scatter(S, nf, p, bin, out, e);
   }
 }
 
@@ -391,37 +665,58 @@ cudaError_t partition_records(const PartArgs& a) {
   const uint32_t B = 1u << a.log2B;
   cudaStream_t st = a.stream;
   const int sms = sm_count();
+  const uint32_t cshift = coarse_shift(a.log2B);
+  const uint32_t C = B >> cshift;
   cudaMemsetAsync(a.cursor, 0, (size_t)B * 4, st);  // the histogram lives in `cursor` until the scan
   cudaMemsetAsync(a.ctrl, 0, 32 * sizeof(uint32_t), st);
-  const uint64_t per_block = (uint64_t)kThreads * kUnroll;
-  const uint64_t blocks = (a.n + per_block - 1) / per_block;
-  int occ_s = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, scatter_kernel, kThreads, 0);
-  const unsigned grid_s = (unsigned)umax64(1, umin64(blocks, (uint64_t)sms * (occ_s > 0 ? occ_s : 1)));
   Pair* pin = static_cast<Pair*>(a.pairs_in_order);
+  const uint64_t segs = coarse_segments(a.n);
+  unsigned G;
+  uint32_t U;
+  int tail_to_first;
   if ((reinterpret_cast<uintptr_t>(a.records) & 15) == 0) {
-    const size_t smem = (size_t)kStages * kTileBytes;
-    cudaFuncSetAttribute(classify_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)kClassifyStages * kTileBytes;
+    cudaFuncSetAttribute(CLASSIFY_TMA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_tma_kernel, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, CLASSIFY_TMA, kClassifyThreads, smem);
     const uint64_t tiles = a.n / kTileRecs;
-    const unsigned grid = (unsigned)umax64(1, umin64(tiles, (uint64_t)sms * (occ > 0 ? occ : 1)));
-    classify_tma_kernel<<<grid, kThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl);
+    G = (unsigned)umin64(segs, umax64(1, umin64(tiles, (uint64_t)sms * (occ > 0 ? occ : 1))));
+    U = kTileRecs;
+    tail_to_first = 1;
+    CLASSIFY_TMA<<<G, kClassifyThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl, cshift,
+                                                    a.seg_hist, (uint32_t)segs);
   } else {
+    const uint64_t per_block = (uint64_t)kThreads * kUnroll;
+    const uint64_t blocks = (a.n + per_block - 1) / per_block;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_kernel, kThreads, 0);
-    const unsigned grid = (unsigned)umax64(1, umin64(blocks, (uint64_t)sms * (occ > 0 ? occ : 1)));
-    classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor);
+    G = (unsigned)umin64(segs, umax64(1, umin64(blocks, (uint64_t)sms * (occ > 0 ? occ : 1))));
+    U = (uint32_t)per_block;
+    tail_to_first = 0;
+    classify_kernel<<<G, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, cshift, a.seg_hist,
+                                            (uint32_t)segs);
   }
   if (a.ev[0]) cudaEventRecord(a.ev[0], st);
   scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, B, a.bin_off, a.cursor, a.ctrl);
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       nullptr);
   if (a.ev[1]) cudaEventRecord(a.ev[1], st);
-  scatter_kernel<<<grid_s, kThreads, 0, st>>>(static_cast<const Pair*>(a.pairs_in_order), a.n, a.cursor,
-                                            static_cast<Pair*>(a.pairs));
+  // two scatter passes through shared memory: coarse bins, then fine bins inside each
+  const uint32_t seg_stride = (uint32_t)segs;
+  coarse_offsets_kernel<<<(C + 7) / 8, 256, 0, st>>>(a.seg_hist, seg_stride, G, C, cshift, a.bin_off, a.ctrl);
+  const size_t smem1 = stage_smem_bytes(C), smem2 = stage_smem_bytes(1u << cshift);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusNone) {
+    cudaFuncSetAttribute(coarse_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
+    cudaFuncSetAttribute(fine_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  }
+  coarse_scatter_kernel<<<G, kStageThreads, smem1, st>>>(pin, a.n, U, tail_to_first, a.seg_hist, seg_stride, cshift,
+                                                          C, static_cast<Pair*>(a.mid), a.ctrl);
+  fine_scatter_kernel<<<C, kStageThreads, smem2, st>>>(static_cast<const Pair*>(a.mid), a.bin_off, B, cshift,
+                                                        static_cast<Pair*>(a.pairs), a.ctrl);
   if (a.ev[2]) cudaEventRecord(a.ev[2], st);
-  *a.launches += 4;
+  *a.launches += 6;
   return cudaGetLastError();
 }
 
@@ -430,17 +725,18 @@ cudaError_t classify_accumulate(const PartArgs& a) {
   const int sms = sm_count();
   Pair* pin = static_cast<Pair*>(a.pairs_in_order);
   if ((reinterpret_cast<uintptr_t>(a.records) & 15) == 0) {
-    const size_t smem = (size_t)kStages * kTileBytes;
-    cudaFuncSetAttribute(classify_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = (size_t)kClassifyStages * kTileBytes;
+    cudaFuncSetAttribute(CLASSIFY_TMA, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, classify_tma_kernel, kThreads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, CLASSIFY_TMA, kClassifyThreads, smem);
     const uint64_t tiles = a.n / kTileRecs;
     const unsigned grid = (unsigned)umax64(1, umin64(tiles, (uint64_t)sms * (occ > 0 ? occ : 1)));
-    classify_tma_kernel<<<grid, kThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl);
+    CLASSIFY_TMA<<<grid, kClassifyThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl, 0,
+                                                       nullptr, 0);
   } else {
     const uint64_t per_block = (uint64_t)kThreads * kUnroll;
     const unsigned grid = (unsigned)umax64(1, umin64((a.n + per_block - 1) / per_block, (uint64_t)sms * 4));
-    classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor);
+    classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, 0, nullptr, 0);
   }
   *a.launches += 1;
   return cudaGetLastError();

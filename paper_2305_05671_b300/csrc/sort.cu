@@ -509,6 +509,7 @@ __device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
 
 __global__ void __launch_bounds__(kThreads, 3) sort_gather_kernel(KArgs k) {
   extern __shared__ __align__(16) uint8_t smem[];
+  if (k.ctrl[kStatusWord]) return;  // partitioning gave up: no item is valid
   const Tile t = carve(smem, k.cap);
   Misc& ms = *t.ms;
   const uint32_t num_items = k.ctrl[kNumItems];
