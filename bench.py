@@ -36,7 +36,7 @@ CPU_SAMPLE = 10_000_000  # records of each key set sorted by the oracle for the 
 # DRAM bytes per record of sort_gather_kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # of one ncu launch divided by its records), from the capture summarised in
 # profiles/sort_gather_kernel_uniform_20M.md; None once the kernel changes.
-SORT_GATHER_TRAFFIC_PER_RECORD = None  # re-captured with ncu after the kernel changes
+SORT_GATHER_TRAFFIC_PER_RECORD = 356.5  # ncu dram bytes per record of sort_gather_kernel, 20M uniform and Zipf (profiles/)
 METRIC = "GB/s sorted (100-B recs), learned+batched vs plain on 1 B300; % HBM roofline"
 
 

@@ -35,7 +35,6 @@ struct Misc {
 // Shared-memory tile of one work item.  Runs are packed as (start << 16) | length.
 struct Tile {
   Pair* A;         // cap pairs
-  uint64_t* E;     // cap base-95 encodings of the first 9 key bytes
   uint32_t* cnt;   // cap digit counters
   uint16_t* perm;  // cap: sorted order being built
   uint16_t* perm2; // cap: scatter target
@@ -64,11 +63,13 @@ struct KArgs {
   int persistent;
 };
 
-// key used by a digit pass: 0 = base-95 encoding (dense for printable keys),
-// 1 = raw key bytes 0-7, 2 = key bytes 8-9 and index.  Encoding order agrees
-// with byte order; equal encodings are split by the raw bytes, then by lo.
+// key used by a digit pass: 0 = base-95 encoding (dense for printable keys;
+// recomputed from the pair, which costs less than the shared memory a cache
+// of it would take from L1), 1 = raw key bytes 0-7, 2 = key bytes 8-9 and
+// index.  Encoding order agrees with byte order; equal encodings are split by
+// the raw bytes, then by lo.
 __device__ __forceinline__ uint64_t sel_key(const Tile& t, uint32_t j, int sel) {
-  return sel == 0 ? t.E[j] : (sel == 1 ? t.A[j].hi : t.A[j].lo);
+  return sel == 0 ? enc9_pair(t.A[j]) : (sel == 1 ? t.A[j].hi : t.A[j].lo);
 }
 
 __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* wsum) {
@@ -249,7 +250,7 @@ __device__ void warp_refine(const Tile& t, uint32_t s0, uint32_t len0) {
   }
 }
 
-// Sort the tile A[0, m) (m <= cap; E filled): on return perm[0, m) lists A in
+// Sort the tile A[0, m) (m <= cap): on return perm[0, m) lists A in
 // (hi, lo) order.  First digit pass block-wide over the whole tile, its short
 // buckets ranked in place by all threads, then the long runs are finished by
 // warps in parallel.
@@ -379,11 +380,7 @@ __device__ __forceinline__ uint32_t merge_split(const Pair* a, uint32_t na, cons
 }
 
 __device__ __forceinline__ void load_tile(const Tile& t, const Pair* src, uint32_t m) {
-  for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
-    const Pair p = src[j];
-    t.A[j] = p;
-    t.E[j] = enc9_pair(p);
-  }
+  for (uint32_t j = threadIdx.x; j < m; j += kThreads) t.A[j] = src[j];
   __syncthreads();
 }
 
@@ -489,8 +486,6 @@ __device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
   uint8_t* p = smem;
   t.A = reinterpret_cast<Pair*>(p);
   p += (size_t)cap * sizeof(Pair);
-  t.E = reinterpret_cast<uint64_t*>(p);
-  p += (size_t)cap * 8;
   t.cnt = reinterpret_cast<uint32_t*>(p);
   p += (size_t)cap * 4;
   t.perm = reinterpret_cast<uint16_t*>(p);
@@ -548,7 +543,7 @@ __global__ void part_items_kernel(const uint32_t* cuts, const uint32_t* item_of_
 
 size_t sort_smem_bytes(uint32_t cap) {
   const size_t stk = (size_t)(cap / kRankMax + 1) * 4;
-  return (size_t)cap * (sizeof(Pair) + 8 + 4 + 2 + 2) + stk * (1 + kWarps) + 16 + sizeof(Misc);
+  return (size_t)cap * (sizeof(Pair) + 4 + 2 + 2) + stk * (1 + kWarps) + 16 + sizeof(Misc);
 }
 
 cudaError_t prepare_sort_kernel(uint32_t cap) {
