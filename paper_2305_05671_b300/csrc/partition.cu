@@ -389,25 +389,27 @@ __global__ void coarse_offsets_kernel(uint32_t* __restrict__ seg, uint32_t seg_s
   }
 }
 
-// Scatter through shared memory: the pairs a CTA holds (PER per thread) are
-// first put in bin order in shared memory (rank inside the batch from a
+// Scatter through shared memory.  A CTA's input pairs arrive by bulk copy
+// (TMA) into one of two input buffers while the previous batch is worked on;
+// a batch is put in bin order in shared memory (rank inside the batch from a
 // shared counter, offsets from a block scan), then written out slot by slot,
 // so the pairs of one bin leave as one contiguous run (whole lines rather
 // than 16-byte pieces scattered over the device).  cur[] holds every bin's
-// next output slot and advances by the batch's counts.
-__device__ __forceinline__ void prefetch_l2_line(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
-
+// next output slot and advances by the batch's counts.  Waits on the copies
+// are bounded like classify's.
 constexpr int kStageThreads = 512;
-constexpr int kStagePer = 8;
-constexpr uint32_t kStagePairs = kStageThreads * kStagePer;  // 4096 pairs = 64 KB
+constexpr int kStagePer = 4;
+constexpr uint32_t kStagePairs = kStageThreads * kStagePer;  // 2048 pairs = 32 KB
 
 struct Stage {
-  Pair* pairs;      // kStagePairs
+  Pair* in[2];      // kStagePairs each: input batches (bulk-copy targets)
+  Pair* pairs;      // kStagePairs: the batch in bin order
   uint16_t* binof;  // kStagePairs
   uint32_t* cnt;    // nb: counts of the batch
   uint32_t* off;    // nb: exclusive offsets in the batch
   uint32_t* cur;    // nb: next output slot
   uint32_t* wsum;   // 33
+  uint64_t* bar;    // 2
 };
 
 __device__ __forceinline__ uint32_t stage_scan(uint32_t v, uint32_t* wsum) {
@@ -477,17 +479,22 @@ __device__ void stage_scatter(const Stage& S, uint32_t nb, const Pair (&p)[kStag
 
 __device__ __forceinline__ Stage carve_stage(uint8_t* smem, uint32_t nb) {
   Stage S;
-  S.pairs = reinterpret_cast<Pair*>(smem);
-  S.binof = reinterpret_cast<uint16_t*>(smem + kStagePairs * sizeof(Pair));
-  uint32_t* w = reinterpret_cast<uint32_t*>(smem + kStagePairs * (sizeof(Pair) + 2));
+  S.in[0] = reinterpret_cast<Pair*>(smem);
+  S.in[1] = S.in[0] + kStagePairs;
+  S.pairs = S.in[1] + kStagePairs;
+  S.binof = reinterpret_cast<uint16_t*>(S.pairs + kStagePairs);
+  uint32_t* w = reinterpret_cast<uint32_t*>(S.binof + kStagePairs);
   S.cnt = w;
   S.off = w + nb;
   S.cur = w + 2 * nb;
   S.wsum = w + 3 * nb;
+  S.bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(w + 3 * nb + 33 + 1) & ~(uintptr_t)7);
   return S;
 }
 
-size_t stage_smem_bytes(uint32_t nb) { return kStagePairs * (sizeof(Pair) + 2) + (3 * (size_t)nb + 33) * 4; }
+size_t stage_smem_bytes(uint32_t nb) {
+  return (size_t)kStagePairs * (3 * sizeof(Pair) + 2) + (3 * (size_t)nb + 33 + 1) * 4 + 2 * 8 + 8;
+}
 
 // Pass B1: pairs (input order) -> coarse-bin order.  CTA b takes the same
 // records as classify's CTA b -- units of U records, unit u to CTA u mod G;
@@ -501,13 +508,18 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
                                                                        const uint32_t* __restrict__ seg,
                                                                        uint32_t seg_stride, uint32_t cshift,
                                                                        uint32_t C, Pair* __restrict__ out,
-                                                                       const uint32_t* ctrl) {
-  extern __shared__ __align__(16) uint8_t smem[];
+                                                                       uint32_t* ctrl) {
+  extern __shared__ __align__(128) uint8_t smem[];
   if (ctrl[kStatusWord]) return;
   const Stage S = carve_stage(smem, C);
   for (uint32_t c = threadIdx.x; c < C; c += kStageThreads) {
     S.cnt[c] = 0;
     S.cur[c] = seg[(size_t)c * seg_stride + blockIdx.x];
+  }
+  if (threadIdx.x == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    fence_mbar_init();
   }
   __syncthreads();
   const uint32_t fmask = (1u << cshift) - 1;
@@ -517,40 +529,85 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
   const bool tail = (n % U) && b == (tail_to_first ? 0 : nfull % G);
   const uint64_t mine = mine_full + (tail ? 1 : 0);  // units of this CTA: b, b+G, ..., then the ragged one
   const uint32_t upb = kStagePairs / U;                // units per batch (U divides kStagePairs)
-  for (uint64_t k0 = 0; k0 < mine; k0 += upb) {
-    {  // the next batch's lines into L2 while this one is staged (one 128-byte line per thread)
-      const uint32_t j = threadIdx.x * 8;
-      const uint64_t ku = k0 + upb + j / U;
-      if (ku < mine_full) prefetch_l2_line(in + (b + ku * G) * U + j % U);
+  const uint64_t nbatch = (mine + upb - 1) / upb;
+  // unit k of this CTA: its first record and its size
+  auto unit_of = [&](uint64_t k, uint64_t* first) -> uint32_t {
+    if (k < mine_full) {
+      *first = (b + k * G) * U;
+      return U;
     }
+    if (k < mine) {
+      *first = nfull * U;
+      return (uint32_t)(n % U);
+    }
+    *first = 0;
+    return 0;
+  };
+  // thread 0: the bulk copies of batch j into input buffer buf (a batch
+  // below nbatch always holds at least one record)
+  auto issue = [&](uint64_t j, int buf) {
+    uint32_t bytes = 0;
+    for (uint32_t u = 0; u < upb; ++u) {
+      uint64_t first;
+      bytes += unit_of(j * upb + u, &first) * (uint32_t)sizeof(Pair);
+    }
+    mbar_expect_tx(&S.bar[buf], bytes);
+    for (uint32_t u = 0; u < upb; ++u) {
+      uint64_t first;
+      const uint32_t c = unit_of(j * upb + u, &first);
+      if (c) bulk_g2s(S.in[buf] + u * U, in + first, c * (uint32_t)sizeof(Pair), &S.bar[buf]);
+    }
+  };
+  uint32_t issued[2] = {0, 0};
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 2; ++q)
+      if ((uint64_t)q < nbatch) {
+        issue(q, q);
+        issued[q] = 1;
+      }
+  for (uint64_t j = 0; j < nbatch; ++j) {
+    const int buf = (int)(j & 1);
+    const bool ok = mbar_wait(&S.bar[buf], (uint32_t)((j >> 1) & 1), kWaitLimitCycles);
     Pair p[kStagePer];
     uint32_t bin[kStagePer];
 #pragma unroll
     for (int k = 0; k < kStagePer; ++k) {
-      const uint32_t j = threadIdx.x + k * kStageThreads;  // place in the batch
-      const uint64_t ku = k0 + j / U;
-      const uint64_t unit = ku < mine_full ? b + ku * G : (ku < mine ? nfull : ~0ull);
-      const uint64_t i = unit == ~0ull ? n : unit * U + j % U;
+      const uint32_t slot = threadIdx.x + k * kStageThreads;
+      uint64_t first;
+      const uint32_t c = unit_of(j * upb + slot / U, &first);
       bin[k] = ~0u;
-      if (i < n) {
-        const Pair q = in[i];
+      if (ok && slot % U < c) {
+        const Pair q = S.in[buf][slot];
         const uint32_t f = (uint32_t)q.lo;
         bin[k] = min(f >> cshift, C - 1);
         p[k].hi = q.hi;
-        p[k].lo = (q.lo & 0x0000FFFF00000000ull) | ((uint64_t)(f & fmask) << 48) | (uint32_t)i;
+        p[k].lo = (q.lo & 0x0000FFFF00000000ull) | ((uint64_t)(f & fmask) << 48) | (uint32_t)(first + slot % U);
       }
+    }
+    if (__syncthreads_or(!ok)) {  // every thread is also done reading input buffer `buf`
+      if (threadIdx.x == 0) {
+        atomicOr(ctrl + kStatusWord, 1u);
+        for (int q = 0; q < 2; ++q)  // copies in flight target this CTA's shared memory: wait, bounded
+          if (issued[q]) mbar_wait(&S.bar[q], (issued[q] - 1) & 1, kWaitLimitCycles);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && j + 2 < nbatch) {
+      fence_proxy_async();
+      issue(j + 2, buf);
+      ++issued[buf];
     }
     stage_scatter(S, C, p, bin, out, n);
   }
 }
 
 // Pass B2: one CTA per coarse bin: its pairs to their fine bins (2^cshift of
-// them), through the same shared-memory staging.
+// them), through the same staging.
 __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pair* __restrict__ in,
                                                                      const uint32_t* __restrict__ bin_off, uint32_t B,
                                                                      uint32_t cshift, Pair* __restrict__ out,
-                                                                     const uint32_t* ctrl) {
-  extern __shared__ __align__(16) uint8_t smem[];
+                                                                     uint32_t* ctrl) {
+  extern __shared__ __align__(128) uint8_t smem[];
   if (ctrl[kStatusWord]) return;
   const uint32_t nf = 1u << cshift;
   const Stage S = carve_stage(smem, nf);
@@ -559,22 +616,56 @@ __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pa
     S.cnt[f] = 0;
     S.cur[f] = bin_off[min(B, f0 + f)];
   }
+  if (threadIdx.x == 0) {
+    mbar_init(&S.bar[0], 1);
+    mbar_init(&S.bar[1], 1);
+    fence_mbar_init();
+  }
   __syncthreads();
   const uint32_t s = bin_off[f0], e = bin_off[min(B, f0 + nf)];
-  for (uint32_t i0 = s; i0 < e; i0 += kStagePairs) {
-    if (i0 + kStagePairs + threadIdx.x * 8 < e) prefetch_l2_line(in + i0 + kStagePairs + threadIdx.x * 8);
+  const uint32_t nbatch = (e - s + kStagePairs - 1) / kStagePairs;
+  auto issue = [&](uint32_t j, int buf) {  // thread 0; a batch below nbatch is never empty
+    const uint32_t i0 = s + j * kStagePairs;
+    const uint32_t bytes = min(kStagePairs, e - i0) * (uint32_t)sizeof(Pair);
+    mbar_expect_tx(&S.bar[buf], bytes);
+    bulk_g2s(S.in[buf], in + i0, bytes, &S.bar[buf]);
+  };
+  uint32_t issued[2] = {0, 0};
+  if (threadIdx.x == 0)
+    for (int q = 0; q < 2; ++q)
+      if ((uint32_t)q < nbatch) {
+        issue(q, q);
+        issued[q] = 1;
+      }
+  for (uint32_t j = 0; j < nbatch; ++j) {
+    const int buf = (int)(j & 1);
+    const bool ok = mbar_wait(&S.bar[buf], (j >> 1) & 1, kWaitLimitCycles);
+    const uint32_t i0 = s + j * kStagePairs;
     Pair p[kStagePer];
     uint32_t bin[kStagePer];
 #pragma unroll
     for (int k = 0; k < kStagePer; ++k) {
-      const uint32_t i = i0 + threadIdx.x + k * kStageThreads;
+      const uint32_t slot = threadIdx.x + k * kStageThreads;
       bin[k] = ~0u;
-      if (i < e) {
-        const Pair q = in[i];
+      if (ok && i0 + slot < e) {
+        const Pair q = S.in[buf][slot];
         bin[k] = (uint32_t)(q.lo >> 48) & (nf - 1);
         p[k].hi = q.hi;
         p[k].lo = q.lo & 0x0000FFFFFFFFFFFFull;
       }
+    }
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) {
+        atomicOr(ctrl + kStatusWord, 1u);
+        for (int q = 0; q < 2; ++q)
+          if (issued[q]) mbar_wait(&S.bar[q], (issued[q] - 1) & 1, kWaitLimitCycles);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && j + 2 < nbatch) {
+      fence_proxy_async();
+      issue(j + 2, buf);
+      ++issued[buf];
     }
     stage_scatter(S, nf, p, bin, out, e);
   }
