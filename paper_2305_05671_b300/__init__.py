@@ -314,10 +314,10 @@ def read_model(d_model, p: Params, n: int):
     import numpy as np
 
     buf = d_model.cpu().numpy()
-    hdr = np.frombuffer(buf[:72].tobytes(), dtype=np.dtype([
+    hdr = np.frombuffer(buf[:96].tobytes(), dtype=np.dtype([
         ("magic", "<u4"), ("kind", "<u4"), ("log2B", "<u4"), ("num_nodes", "<u4"), ("S", "<u8"), ("node_cap", "<u8"),
         ("nodes_off", "<u8"), ("splitters_off", "<u8"), ("bytes", "<u8"), ("T", "<u4"), ("Dmax", "<u4"),
-        ("levels", "<u4"), ("fallback", "<u4")]))[0]
+        ("levels", "<u4"), ("fallback", "<u4"), ("lut_off", "<u8"), ("knots_off", "<u8"), ("weights_off", "<u8")]))[0]
     ndt = np.dtype([("s", "<u4"), ("e", "<u4"), ("base", "<u8"), ("child0", "<u4"), ("fanout", "<u4"),
                     ("shift", "<u4"), ("depth_set", "<u4"), ("a", "<f8"), ("b", "<f8"), ("c", "<f8"), ("h", "<f8")])
     nn = int(hdr["num_nodes"])
@@ -327,12 +327,7 @@ def read_model(d_model, p: Params, n: int):
     B = 1 << int(hdr["log2B"])
     spl = np.frombuffer(buf[so:so + 8 * B].tobytes(), dtype=np.uint64)
     h = {k: hdr[k].item() for k in hdr.dtype.names}
-    # after the splitters: the radix index, then the network's knots and weights
-    up = lambda v: (v + 255) & ~255
-    lut_off = so + up(8 * B)
-    cells = ((95**9 - 1) >> 42) + 2
-    knots_off = lut_off + up(4 * cells)
-    w_off = knots_off + 256
-    h["mlp_knots"] = np.frombuffer(buf[knots_off:knots_off + 104].tobytes(), dtype=np.uint64).copy()
-    h["mlp_w"] = np.frombuffer(buf[w_off:w_off + 1505 * 4].tobytes(), dtype=np.float32).copy()
+    ko, wo = int(hdr["knots_off"]), int(hdr["weights_off"])
+    h["mlp_knots"] = np.frombuffer(buf[ko:ko + 104].tobytes(), dtype=np.uint64).copy()
+    h["mlp_w"] = np.frombuffer(buf[wo:wo + 1505 * 4].tobytes(), dtype=np.float32).copy()
     return h, nodes, spl

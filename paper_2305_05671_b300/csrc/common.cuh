@@ -47,6 +47,7 @@ struct ModelHeader {
   uint64_t S, node_cap;
   uint64_t nodes_off, splitters_off, bytes;
   uint32_t T, Dmax, levels, fallback;
+  uint64_t lut_off, knots_off, weights_off;  // radix index, the network's knots and weights
 };
 
 // The k-th output of the SplitMix64 generator seeded with `seed` (Steele,
@@ -103,15 +104,51 @@ __device__ __forceinline__ Pair load_pair(const uint8_t* rec, uint32_t idx) {
 }
 
 // ---------------------------------------------------------------- radix index of the splitters
-// lut[c] = largest q with t[q] <= c << kFineLutShift, for c in [0, kFineLutCells)
+// Cell c covers encodings [c << kFineLutShift, (c + 1) << kFineLutShift).
+// Level 1 (uint2 per cell): .x = largest q with t[q] <= c << kFineLutShift;
+// .y = 0, or, for a cell holding more than kLutDense splitters,
+// (offset << 5) | nb: the cell is split into 2^nb sub-cells whose level-2
+// entries lut2[offset + k] (k = 0..2^nb) hold the largest q with t[q] <= the
+// sub-cell's start.  Either way the answer for x lies in [lo, hi] of x's cell
+// or sub-cell, and a short binary search finishes it.  The level-2 table
+// lives right after level 1 (kFineLutCells uint2 entries).
 constexpr int kFineLutShift = 42;
 constexpr uint32_t kFineLutCells = (uint32_t)((kEncTop - 1) >> kFineLutShift) + 2;
+constexpr uint32_t kLutDense = 4;      // cells with more splitters get a level-2 split
+constexpr uint32_t kLutMaxBits = 14;   // at most 2^14 sub-cells per cell
+constexpr uint32_t kLutOversplit = 2;  // sub-cells = 4 x the cell's splitters rounded up to a power of two
+// Level-2 capacity for 2^log2B splitters: a dense cell with cnt splitters
+// takes 2^nb + 1 < 8 cnt + 1 words and at most B/5 cells are dense, so
+// 8B + B/4 words hold every split; 256 more at the end hold the scan's block
+// totals while the index is built.
+inline size_t lut_level2_words(uint32_t log2B) {
+  const size_t B = (size_t)1 << log2B;
+  return 8 * B + B / 4 + 256;
+}
+// words of the whole index (level 1 and level 2)
+inline size_t lut_words_for(uint32_t log2B) { return 2 * (size_t)kFineLutCells + lut_level2_words(log2B); }
+
+// [lo, hi]: the search range of splitter indices for x
+__device__ __forceinline__ void lut_range(const uint32_t* __restrict__ lut, uint64_t x, uint32_t& lo, uint32_t& hi) {
+  const uint2* l1 = reinterpret_cast<const uint2*>(lut);
+  const uint32_t c = (uint32_t)(x >> kFineLutShift);
+  const uint2 a = __ldg(l1 + c), b = __ldg(l1 + c + 1);
+  lo = a.x;
+  hi = b.x;
+  if (a.y) {
+    const uint32_t nb = a.y & 31, off = a.y >> 5;
+    const uint32_t k = (uint32_t)(x >> (kFineLutShift - nb)) & ((1u << nb) - 1);
+    const uint32_t* l2 = lut + 2 * kFineLutCells + off;
+    lo = __ldg(l2 + k);
+    hi = __ldg(l2 + k + 1);
+  }
+}
 
 // q = largest j with t[j] <= x, via the radix index then a binary search
 __device__ __forceinline__ uint32_t splitter_search(const uint64_t* __restrict__ t, const uint32_t* __restrict__ lut,
                                                     uint64_t x) {
-  const uint32_t c = (uint32_t)(x >> kFineLutShift);
-  uint32_t lo = __ldg(lut + c), hi = __ldg(lut + c + 1);
+  uint32_t lo, hi;
+  lut_range(lut, x, lo, hi);
   while (lo < hi) {
     const uint32_t mid = (lo + hi + 1) >> 1;
     if (__ldg(t + mid) <= x) lo = mid;
@@ -217,6 +254,7 @@ inline size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T) { return m
 // fits the RMI; *sorted_out = the buffer holding the sorted sample (a.samp or a.samp + S)
 cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sorted_out);
 cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, uint64_t* out, cudaStream_t st);
+// builds both levels of the radix index (scratch: kFineLutCells words)
 cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* lut, cudaStream_t st);
 cudaError_t set_model_kind(void* model, uint32_t kind, uint32_t fallback, cudaStream_t st);
 

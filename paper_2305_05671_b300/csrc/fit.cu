@@ -481,14 +481,103 @@ __global__ void splitter_batch_kernel(const DNode* __restrict__ nodes, uint32_t 
   }
 }
 
-// radix index of the splitters: cells c with t[q] <= c << 42 < t[q+1] hold q
-__global__ void fine_lut_kernel(const uint64_t* __restrict__ t, uint32_t log2B, uint32_t* __restrict__ lut) {
+// radix index of the splitters, level 1: cells c with t[q] <= c << 42 < t[q+1] hold q
+__global__ void fine_lut_kernel(const uint64_t* __restrict__ t, uint32_t log2B, uint2* __restrict__ lut) {
   const uint32_t B = 1u << log2B;
   const uint64_t cell = 1ull << kFineLutShift;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < B; q += gridDim.x * blockDim.x) {
     const uint64_t c0 = (t[q] + cell - 1) >> kFineLutShift;
     const uint64_t c1 = q + 1 < B ? (t[q + 1] + cell - 1) >> kFineLutShift : (uint64_t)kFineLutCells;
-    for (uint64_t c = c0; c < c1 && c < kFineLutCells; ++c) lut[c] = q;
+    for (uint64_t c = c0; c < c1 && c < kFineLutCells; ++c) lut[c] = make_uint2(q, 0u);
+  }
+}
+
+// level-2 sub-cells of a cell holding cnt splitters (0 = no split)
+__device__ __forceinline__ uint32_t lut_split_bits(uint32_t cnt) {
+  if (cnt <= kLutDense) return 0;
+  const uint32_t b = (32 - __clz(cnt - 1)) + kLutOversplit;  // ceil(log2 cnt) + oversplit
+  return b < kLutMaxBits ? b : kLutMaxBits;
+}
+
+// level-2 sizes (2^nb + 1 per dense cell): per block of 1024 cells, their total
+__device__ __forceinline__ uint32_t lut_cell_bits(const uint2* lut, uint32_t c) {
+  return c + 1 < kFineLutCells ? lut_split_bits(lut[c + 1].x - lut[c].x) : 0u;
+}
+__device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t* wsum) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  if (lane == 0) wsum[warp] = v;
+  __syncthreads();
+  uint32_t t = 0;
+  for (int w = 0; w < 32; ++w) t += wsum[w];
+  return t;
+}
+__global__ void __launch_bounds__(1024) lut_block_sizes_kernel(const uint2* __restrict__ lut, uint32_t* __restrict__ part) {
+  __shared__ uint32_t wsum[32];
+  const uint32_t c = blockIdx.x * 1024 + threadIdx.x;
+  const uint32_t nb = c < kFineLutCells ? lut_cell_bits(lut, c) : 0;
+  const uint32_t t = block_sum_1024(nb ? (1u << nb) + 1 : 0, wsum);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// level-2 offsets: exclusive scan of the sizes (block carry from the block
+// totals before it), written into the cells' .y as (offset << 5) | nb
+__global__ void __launch_bounds__(1024) lut_offsets_kernel(uint2* __restrict__ lut, const uint32_t* __restrict__ part) {
+  __shared__ uint32_t wsum[33];
+  __shared__ uint32_t carry_sh;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x < 32) {
+    uint32_t s = 0;
+    for (uint32_t b = lane; b < blockIdx.x; b += 32) s += part[b];
+    for (int d = 16; d; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) carry_sh = s;
+  }
+  const uint32_t c = blockIdx.x * 1024 + threadIdx.x;
+  const uint32_t nb = c < kFineLutCells ? lut_cell_bits(lut, c) : 0;
+  const uint32_t v = nb ? (1u << nb) + 1 : 0;
+  uint32_t incl = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= (uint32_t)d) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const uint32_t w = wsum[lane];
+    uint32_t wi = w;
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= (uint32_t)d) wi += y;
+    }
+    wsum[lane] = wi - w;
+  }
+  __syncthreads();
+  // every block reads its cells' .x before any block writes .y: the two are
+  // separate words, so the reads of the neighbours' .x stay valid
+  if (c < kFineLutCells) lut[c].y = nb ? ((carry_sh + wsum[warp] + incl - v) << 5) | nb : 0u;
+}
+
+// level-2 entries: a warp per dense cell, lanes over its sub-cell starts;
+// entry k = largest q in the cell's range with t[q] <= the sub-cell's start
+__global__ void lut_fill_kernel(const uint64_t* __restrict__ t, const uint2* __restrict__ lut, uint32_t* __restrict__ l2) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c + 1 < kFineLutCells; c += warps) {
+    const uint2 a = lut[c];
+    if (!a.y) continue;
+    const uint32_t nb = a.y & 31, off = a.y >> 5;
+    const uint32_t q0 = a.x, q1 = lut[c + 1].x;
+    const uint64_t start = (uint64_t)c << kFineLutShift;
+    for (uint32_t k = lane; k <= (1u << nb); k += 32) {
+      const uint64_t v = start + ((uint64_t)k << (kFineLutShift - nb));
+      uint32_t lo = q0, hi = q1;  // t[q0] <= v, answer <= q1
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (t[mid] <= v) lo = mid;
+        else hi = mid - 1;
+      }
+      l2[off + k] = lo;
+    }
   }
 }
 
@@ -515,7 +604,7 @@ ModelLayout model_layout(uint64_t S, uint32_t log2B, uint32_t T) {
   L.splitters = o;
   o += up((size_t)8 << log2B);
   L.lut = o;
-  o += up((size_t)kFineLutCells * 4);
+  o += up(lut_words_for(log2B) * 4);
   L.mlp_knots = o;
   o += 256;
   L.mlp_w = o;
@@ -544,7 +633,14 @@ cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t
 
 cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* lut, cudaStream_t st) {
   const uint32_t B = 1u << log2B;
-  fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, log2B, lut);
+  uint2* l1 = reinterpret_cast<uint2*>(lut);
+  fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, log2B, l1);
+  const uint32_t blocks = (kFineLutCells + 1023) / 1024;
+  // block totals go to the last 256 words of level 2, which the entries never reach
+  uint32_t* part = lut + 2 * kFineLutCells + lut_level2_words(log2B) - 256;
+  lut_block_sizes_kernel<<<blocks, 1024, 0, st>>>(l1, part);
+  lut_offsets_kernel<<<blocks, 1024, 0, st>>>(l1, part);
+  lut_fill_kernel<<<(kFineLutCells + 7) / 8, 256, 0, st>>>(splitters, l1, lut + 2 * kFineLutCells);
   return cudaGetLastError();
 }
 
@@ -613,6 +709,9 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sort
   h.nodes_off = ml.nodes;
   h.splitters_off = ml.splitters;
   h.bytes = ml.bytes;
+  h.lut_off = ml.lut;
+  h.knots_off = ml.mlp_knots;
+  h.weights_off = ml.mlp_w;
   h.T = a.T;
   h.Dmax = a.Dmax;
   DNode* nodes = reinterpret_cast<DNode*>(mb + h.nodes_off);
@@ -664,7 +763,7 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sort
   // 4. splitters of the fine bins
   const uint32_t B = 1u << a.log2B;
   splitter_kernel<<<(B + 127) / 128, 128, 0, st>>>(nodes, a.log2B, splitters);
-  fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut));
+  build_fine_lut(splitters, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut), st);
   write_header<<<1, 1, 0, st>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
   L += 3;
   *nodes_out = nodes_total;

@@ -114,10 +114,8 @@ __global__ void __launch_bounds__(NT) classify_tma_kernel(const uint8_t* __restr
       const int slot = threadIdx.x + j * NT, s = slot / kTileRecs;
       pr[j] = pair_from_words(w[j][0], w[j][1], w[j][2]);
       x[j] = enc9_pair(pr[j]);
-      const uint32_t c = (uint32_t)(x[j] >> kFineLutShift);
-      const bool v = k0 + s * G < ntiles;
-      lo[j] = v ? __ldg(lut + c) : 0;
-      hi[j] = v ? __ldg(lut + c + 1) : 0;
+      lo[j] = hi[j] = 0;
+      if (k0 + s * G < ntiles) lut_range(lut, x[j], lo[j], hi[j]);
     }
     for (;;) {
       bool more = false;
