@@ -272,3 +272,22 @@ def test_full_size_100M(wl):
     assert np.array_equal(part_off.cpu().numpy().astype(np.uint64), off)
     assert oracle.validate(host_in, host_out) == 0
     assert np.diff(off.astype(np.int64)).max() / (n / P) <= 1.1
+
+
+@pytest.mark.parametrize("n", [1000, 70_001, 600_003])
+@pytest.mark.parametrize("in_off,out_off", [(4, 0), (0, 4), (12, 8)])
+def test_unaligned_record_buffers(n, in_off, out_off):
+    """Records at 4-byte but not 16-byte alignment take the plain-load
+    classify (2048-record units per CTA, the ragged unit on its own CTA) and
+    an output buffer whose pair scratch starts past its first bytes."""
+    host = recgen.generate_cpu(n, SPECS["zipf11"])
+    big_in = torch.zeros(n * 100 + 16, dtype=torch.uint8, device="cuda")
+    big_out = torch.zeros(n * 100 + 16, dtype=torch.uint8, device="cuda")
+    d_in = big_in[in_off:in_off + n * 100]
+    d_out = big_out[out_off:out_off + n * 100]
+    d_in.copy_(torch.from_numpy(host).cuda())
+    elsar.sort(d_in, d_out, n, elsar.Params(num_partitions=64, seed=n))
+    torch.cuda.synchronize()
+    assert np.array_equal(d_out.cpu().numpy(), oracle.stable_sort(host))
+    # the bytes around the output are untouched
+    assert int(big_out[:out_off].sum()) == 0 and int(big_out[out_off + n * 100:].sum()) == 0
