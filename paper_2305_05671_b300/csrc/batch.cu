@@ -175,8 +175,8 @@ struct Tuning {
 size_t up(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct BatchLayout {
-  size_t ctrl, ins, outs, n, sets, log2B, tbase, poff, sp0, sp1, x, pnode, nodes, sums, fc, t, pairsA, pairsB, bin_off,
-      cursor, items, item_flag, oversize, total;
+  size_t ctrl, ins, outs, n, sets, log2B, tbase, poff, sp0, sp1, x, pnode, nodes, sums, fc, t, pairsA, pairsB, seg,
+      bin_off, cursor, items, item_flag, oversize, total;
   uint64_t S_total, B_total, N_total, node_cap;
 };
 
@@ -218,6 +218,7 @@ BatchLayout batch_layout(const uint64_t* n, uint32_t K, const Tuning& tu, uint32
   L.t = take(B * 8);
   L.pairsA = take(N * sizeof(Pair));
   L.pairsB = take(N * sizeof(Pair));
+  L.seg = take(coarse_segments(N) * kMaxCoarse * 4);
   L.bin_off = take((B + 1) * 4);
   L.cursor = take(B * 4);
   L.items = take((B + 1) * 4);
@@ -376,6 +377,8 @@ cudaError_t enqueue(elsar_batch& b, cudaStream_t st) {
   pa.log2B = at<uint32_t>(ws, L.log2B);
   pa.pairs_in_order = at<Pair>(ws, L.pairsA);
   pa.pairs = at<Pair>(ws, L.pairsB);
+  pa.N = L.N_total;
+  pa.seg_hist = at<uint32_t>(ws, L.seg);
   pa.bin_off = at<uint32_t>(ws, L.bin_off);
   pa.cursor = at<uint32_t>(ws, L.cursor);
   pa.items = at<uint32_t>(ws, L.items);
@@ -419,6 +422,7 @@ cudaError_t build_graph(elsar_batch& b, cudaStream_t st) {
   cudaError_t e = upload_tables(b, st);
   if (e != cudaSuccess) return e;
   if ((e = prepare_sort_kernel(b.tune.cap)) != cudaSuccess) return e;
+  if ((e = prepare_scatter_kernels()) != cudaSuccess) return e;
   if ((e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
   cudaError_t qe = enqueue(b, st);
   e = cudaStreamEndCapture(st, &b.graph);

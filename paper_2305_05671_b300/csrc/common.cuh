@@ -284,6 +284,8 @@ struct PartArgs {
 // Two-pass scatter: coarse bins of 2^coarse_shift(log2B) fine bins, at most
 // kMaxCoarse of them; classify CTAs (at most kMaxSegments) count per coarse bin.
 constexpr uint32_t kMaxCoarse = 512;
+constexpr uint32_t kMaxFineShift = 11;    // at most 2^11 fine bins per coarse bin (shared-memory cursors)
+constexpr uint32_t kStagedMaxShift = 9;   // above 2^9 fine bins per coarse bin the runs get too short to stage
 constexpr uint32_t kMaxSegments = 2048;
 inline uint32_t coarse_shift(uint32_t log2B) { return log2B > 9 ? log2B - 9 : 0; }
 inline uint64_t coarse_segments(uint64_t n) {
@@ -303,8 +305,10 @@ struct BatchPartArgs {
   const uint64_t* splitters;  // B
   const uint64_t* tbase;      // K+1
   const uint32_t* log2B;      // K
-  Pair* pairs_in_order;
-  Pair* pairs;
+  uint64_t N;               // records of all sets
+  Pair* pairs_in_order;     // N pairs scratch
+  Pair* pairs;              // N pairs: bin-ordered output
+  uint32_t* seg_hist;       // coarse_segments(N) x kMaxCoarse
   uint32_t* bin_off;  // B+1
   uint32_t* cursor;   // B
   uint32_t* items;    // B+1
@@ -315,6 +319,8 @@ struct BatchPartArgs {
   uint32_t* launches;
 };
 cudaError_t partition_batch(const BatchPartArgs& a);
+// the scatter passes' shared-memory limit (call before graph capture)
+cudaError_t prepare_scatter_kernels();
 
 struct SortArgs {
   const uint8_t* records;

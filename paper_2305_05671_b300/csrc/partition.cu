@@ -387,6 +387,16 @@ __global__ void coarse_offsets_kernel(uint32_t* __restrict__ seg, uint32_t seg_s
   }
 }
 
+__device__ __forceinline__ uint32_t upper_set(const uint64_t* __restrict__ off, uint32_t K, uint64_t g) {
+  uint32_t lo = 0, hi = K - 1;  // largest k with off[k] <= g
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (off[mid] <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
 // Scatter through shared memory.  A CTA's input pairs arrive by bulk copy
 // (TMA) into one of two input buffers while the previous batch is worked on;
 // a batch is put in bin order in shared memory (rank inside the batch from a
@@ -494,7 +504,9 @@ size_t stage_smem_bytes(uint32_t nb) {
   return (size_t)kStagePairs * (3 * sizeof(Pair) + 2) + (3 * (size_t)nb + 33 + 1) * 4 + 2 * 8 + 8;
 }
 
-// Pass B1: pairs (input order) -> coarse-bin order.  CTA b takes the same
+// Pass B1: pairs (input order) -> coarse-bin order.  With K record sets
+// (poff non-null) the index written is the one inside the record's set.
+// CTA b takes the same
 // records as classify's CTA b -- units of U records, unit u to CTA u mod G;
 // the ragged last unit to CTA 0 (TMA classify) or to its own CTA (plain
 // classify) -- so its counts per coarse bin are the ones classify wrote, and
@@ -506,7 +518,8 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
                                                                        const uint32_t* __restrict__ seg,
                                                                        uint32_t seg_stride, uint32_t cshift,
                                                                        uint32_t C, Pair* __restrict__ out,
-                                                                       uint32_t* ctrl) {
+                                                                       uint32_t* ctrl, const uint64_t* __restrict__ poff,
+                                                                       uint32_t K) {
   extern __shared__ __align__(128) uint8_t smem[];
   if (ctrl[kStatusWord]) return;
   const Stage S = carve_stage(smem, C);
@@ -579,7 +592,9 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
         const uint32_t f = (uint32_t)q.lo;
         bin[k] = min(f >> cshift, C - 1);
         p[k].hi = q.hi;
-        p[k].lo = (q.lo & 0x0000FFFF00000000ull) | ((uint64_t)(f & fmask) << 48) | (uint32_t)(first + slot % U);
+        const uint64_t g = first + slot % U;  // the record's place in the input (all sets together)
+        const uint64_t i = poff ? g - poff[upper_set(poff, K, g)] : g;
+        p[k].lo = (q.lo & 0x0000FFFF00000000ull) | ((uint64_t)(f & fmask) << 48) | (uint32_t)i;
       }
     }
     if (__syncthreads_or(!ok)) {  // every thread is also done reading input buffer `buf`
@@ -670,15 +685,6 @@ __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pa
 }
 
 // ---------------------------------------------------------------- many record sets at once
-__device__ __forceinline__ uint32_t upper_set(const uint64_t* __restrict__ off, uint32_t K, uint64_t g) {
-  uint32_t lo = 0, hi = K - 1;  // largest k with off[k] <= g
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= g) lo = mid;
-    else hi = mid - 1;
-  }
-  return lo;
-}
 
 // Pass A over K record sets: record i of set k goes to global pair slot
 // poff[k] + i with the set's fine bin tbase[k] + q (binary search over the
@@ -688,7 +694,12 @@ __global__ void __launch_bounds__(kThreads) classify_batch_kernel(const uint8_t*
                                                                   const uint64_t* __restrict__ t,
                                                                   const uint64_t* __restrict__ tbase,
                                                                   const uint32_t* __restrict__ log2B,
-                                                                  Pair* __restrict__ pairs, uint32_t* __restrict__ hist) {
+                                                                  Pair* __restrict__ pairs, uint32_t* __restrict__ hist,
+                                                                  uint32_t cshift, uint32_t* __restrict__ seg_hist,
+                                                                  uint32_t seg_stride) {
+  __shared__ uint32_t hc[kMaxCoarse];  // this CTA's counts per coarse bin (units of 256 records)
+  for (uint32_t c = threadIdx.x; c < kMaxCoarse; c += kThreads) hc[c] = 0;
+  __syncthreads();
   const uint64_t N = poff[K];
   for (uint64_t g = blockIdx.x * (uint64_t)kThreads + threadIdx.x; g < N; g += (uint64_t)gridDim.x * kThreads) {
     const uint32_t k = upper_set(poff, K, g);
@@ -706,22 +717,31 @@ __global__ void __launch_bounds__(kThreads) classify_batch_kernel(const uint8_t*
     p.lo |= q;
     pairs[g] = p;
     atomicAdd(hist + q, 1u);
+    if (seg_hist) atomicAdd(&hc[min(q >> cshift, kMaxCoarse - 1)], 1u);
+  }
+  if (seg_hist) {
+    __syncthreads();
+    for (uint32_t c = threadIdx.x; c < kMaxCoarse; c += kThreads) seg_hist[c * seg_stride + blockIdx.x] = hc[c];
   }
 }
 
-// Pass B over K record sets: the pair's index becomes the index within its set.
-__global__ void __launch_bounds__(kThreads) scatter_batch_kernel(const Pair* __restrict__ in,
-                                                                 const uint64_t* __restrict__ poff, uint32_t K,
-                                                                 uint32_t* __restrict__ cursor, Pair* __restrict__ out) {
-  const uint64_t N = poff[K];
+// Pass B in one step, for fine-bin spaces too large for the two staged
+// passes to write whole runs (more than 2^kStagedMaxShift fine bins per
+// coarse bin): slot from an atomic cursor per bin; the record index (inside
+// its set when poff is given) replaces the fine bin.
+__global__ void __launch_bounds__(kThreads) scatter_atomic_kernel(const Pair* __restrict__ in, uint64_t N,
+                                                                  const uint64_t* __restrict__ poff, uint32_t K,
+                                                                  uint32_t* __restrict__ cursor, Pair* __restrict__ out,
+                                                                  const uint32_t* ctrl) {
+  if (ctrl[kStatusWord]) return;
   for (uint64_t g = blockIdx.x * (uint64_t)kThreads + threadIdx.x; g < N; g += (uint64_t)gridDim.x * kThreads) {
     const Pair p = in[g];
     const uint32_t slot = atomicAdd(cursor + (uint32_t)p.lo, 1u);
-    const uint32_t k = upper_set(poff, K, g);
+    const uint64_t i = poff ? g - poff[upper_set(poff, K, g)] : g;
     Pair o;
     o.hi = p.hi;
-    o.lo = (p.lo & 0xFFFFFFFF00000000ull) | (uint32_t)(g - poff[k]);
-    out[slot] = o;
+    o.lo = (p.lo & 0xFFFFFFFF00000000ull) | (uint32_t)i;
+    if (slot < N) out[slot] = o;
   }
 }
 
@@ -733,20 +753,56 @@ __global__ void mark_set_starts(const uint64_t* __restrict__ tbase, uint32_t K, 
 
 }  // namespace
 
+cudaError_t prepare_scatter_kernels() {
+  const int smem = (int)stage_smem_bytes(1u << kMaxFineShift);  // the largest bin count a pass takes
+  cudaError_t e = cudaFuncSetAttribute(coarse_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fine_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return e;
+}
+
+// coarse bins over a fine-bin space of B bins: 2^cshift fine bins each, at most kMaxCoarse
+static void coarse_of(uint64_t B, uint32_t* cshift, uint32_t* C) {
+  uint32_t s = 0;
+  while (((B + (1ull << s) - 1) >> s) > kMaxCoarse) ++s;
+  *cshift = s;
+  *C = (uint32_t)((B + (1ull << s) - 1) >> s);
+}
+
 cudaError_t partition_batch(const BatchPartArgs& a) {
   cudaStream_t st = a.stream;
   const int sms = sm_count();
   cudaMemsetAsync(a.cursor, 0, (size_t)a.B * 4, st);
   cudaMemsetAsync(a.ctrl, 0, 32 * sizeof(uint32_t), st);
   cudaMemsetAsync(a.item_flag, 0, (size_t)a.B * 4, st);
-  const unsigned grid = (unsigned)sms * 8;
-  classify_batch_kernel<<<grid, kThreads, 0, st>>>(a.ins, a.poff, a.K, a.splitters, a.tbase, a.log2B, a.pairs_in_order,
-                                                  a.cursor);
+  uint32_t cshift, C;
+  coarse_of(a.B, &cshift, &C);
+  const uint64_t segs = coarse_segments(a.N);
+  const unsigned G = (unsigned)umin64(segs, (uint64_t)sms * 8);
+  if (cshift > kStagedMaxShift) {  // bins too many for whole runs: one atomic pass
+    classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.poff, a.K, a.splitters, a.tbase, a.log2B,
+                                                 a.pairs_in_order, a.cursor, 0, nullptr, 0);
+    scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
+    scatter_atomic_kernel<<<G, kThreads, 0, st>>>(a.pairs_in_order, a.N, a.poff, a.K, a.cursor, a.pairs, a.ctrl);
+    mark_set_starts<<<(a.K + 255) / 256, 256, 0, st>>>(a.tbase, a.K, a.item_flag);
+    items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize,
+                                             a.ctrl);
+    *a.launches += 5;
+    return cudaGetLastError();
+  }
+  // roles: input-order pairs and the final bin order share `pairs`; the
+  // coarse order between the two passes lives in `pairs_in_order`
+  classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.poff, a.K, a.splitters, a.tbase, a.log2B, a.pairs, a.cursor,
+                                               cshift, a.seg_hist, (uint32_t)segs);
   scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
-  scatter_batch_kernel<<<grid, kThreads, 0, st>>>(a.pairs_in_order, a.poff, a.K, a.cursor, a.pairs);
+  coarse_offsets_kernel<<<(C + 7) / 8, 256, 0, st>>>(a.seg_hist, (uint32_t)segs, G, C, cshift, a.bin_off, a.ctrl);
+  coarse_scatter_kernel<<<G, kStageThreads, stage_smem_bytes(C), st>>>(a.pairs, a.N, kThreads, 0, a.seg_hist,
+                                                                        (uint32_t)segs, cshift, C, a.pairs_in_order,
+                                                                        a.ctrl, a.poff, a.K);
+  fine_scatter_kernel<<<C, kStageThreads, stage_smem_bytes(1u << cshift), st>>>(a.pairs_in_order, a.bin_off, a.B,
+                                                                                 cshift, a.pairs, a.ctrl);
   mark_set_starts<<<(a.K + 255) / 256, 256, 0, st>>>(a.tbase, a.K, a.item_flag);
   items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize, a.ctrl);
-  *a.launches += 5;
+  *a.launches += 7;
   return cudaGetLastError();
 }
 
@@ -790,18 +846,22 @@ cudaError_t partition_records(const PartArgs& a) {
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       nullptr);
   if (a.ev[1]) cudaEventRecord(a.ev[1], st);
+  if (cshift > kStagedMaxShift) {  // bins too many for whole runs: one atomic pass
+    scatter_atomic_kernel<<<(unsigned)sms * 8, kThreads, 0, st>>>(pin, a.n, nullptr, 0, a.cursor,
+                                                                static_cast<Pair*>(a.pairs), a.ctrl);
+    if (a.ev[2]) cudaEventRecord(a.ev[2], st);
+    *a.launches += 4;
+    return cudaGetLastError();
+  }
   // two scatter passes through shared memory: coarse bins, then fine bins inside each
   const uint32_t seg_stride = (uint32_t)segs;
   coarse_offsets_kernel<<<(C + 7) / 8, 256, 0, st>>>(a.seg_hist, seg_stride, G, C, cshift, a.bin_off, a.ctrl);
   const size_t smem1 = stage_smem_bytes(C), smem2 = stage_smem_bytes(1u << cshift);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);
-  if (cs == cudaStreamCaptureStatusNone) {
-    cudaFuncSetAttribute(coarse_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem1);
-    cudaFuncSetAttribute(fine_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-  }
+  if (cs == cudaStreamCaptureStatusNone) prepare_scatter_kernels();
   coarse_scatter_kernel<<<G, kStageThreads, smem1, st>>>(pin, a.n, U, tail_to_first, a.seg_hist, seg_stride, cshift,
-                                                          C, static_cast<Pair*>(a.mid), a.ctrl);
+                                                          C, static_cast<Pair*>(a.mid), a.ctrl, nullptr, 0);
   fine_scatter_kernel<<<C, kStageThreads, smem2, st>>>(static_cast<const Pair*>(a.mid), a.bin_off, B, cshift,
                                                         static_cast<Pair*>(a.pairs), a.ctrl);
   if (a.ev[2]) cudaEventRecord(a.ev[2], st);
