@@ -127,20 +127,21 @@ class Clocks:
 
 
 def cpu_baseline(args, world_rank=0):
-    """The oracle, as it stands, on a bounded sample of each key set (first CPU_SAMPLE records)."""
+    """The oracle, as it stands, on a bounded sample of each key set (the first --cpu-sample records)."""
     import oracle
     import recgen
 
+    m = args.cpu_sample
     tot_bytes, tot_s = 0, 0.0
     for wl in workloads():
-        host = recgen.generate_cpu(wl["n"], wl["spec"], i0=0, count=CPU_SAMPLE)
-        log2B = oracle.default_fine_log2(CPU_SAMPLE, PARTITIONS)
+        host = recgen.generate_cpu(wl["n"], wl["spec"], i0=0, count=m)
+        log2B = oracle.default_fine_log2(m, PARTITIONS)
         t0 = time.perf_counter()
-        oracle.sort(host, PARTITIONS, log2B, S=oracle.default_sample_size(CPU_SAMPLE), seed=0x5EED, balance=1)
+        oracle.sort(host, PARTITIONS, log2B, S=oracle.default_sample_size(m), seed=0x5EED, balance=1)
         tot_s += time.perf_counter() - t0
-        tot_bytes += CPU_SAMPLE * RECORD
+        tot_bytes += m * RECORD
     return {"value": round(tot_bytes / tot_s / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {CPU_SAMPLE:,} records of each of the two 100M-record key sets, oracle sort "
+            "sample": f"first {m:,} records of each of the two 100M-record key sets, oracle sort "
                       f"(1024 partitions, 1% sample), single-threaded"}
 
 
@@ -434,6 +435,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE, help="records of each set the oracle sorts")
     ap.add_argument("--records", type=int, default=N_RECORDS, help="records per key set (profiling cases use fewer)")
     ap.add_argument("--sets", default="uniform,zipf", help="key sets to sort per step")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
