@@ -105,15 +105,18 @@ __device__ __forceinline__ Pair load_pair(const uint8_t* rec, uint32_t idx) {
 
 // ---------------------------------------------------------------- radix index of the splitters
 // Cell c covers encodings [c << kFineLutShift, (c + 1) << kFineLutShift).
-// Level 1 (uint2 per cell): .x = largest q with t[q] <= c << kFineLutShift;
-// .y = 0, or, for a cell holding more than kLutDense splitters,
+// Level 1 (uint4 per cell): .x = q, the largest index with t[q] <= c <<
+// kFineLutShift; .z/.w = the low and high words of t[q + 1] (95^9 past the
+// last splitter), so a cell holding one splitter is resolved by its own
+// entry; .y = 0, or, for a cell holding more than kLutDense splitters,
 // (offset << 5) | nb: the cell is split into 2^nb sub-cells whose level-2
 // entries lut2[offset + k] (k = 0..2^nb) hold the largest q with t[q] <= the
 // sub-cell's start.  Either way the answer for x lies in [lo, hi] of x's cell
 // or sub-cell, and a short binary search finishes it.  The level-2 table
-// lives right after level 1 (kFineLutCells uint2 entries).
+// lives right after level 1 (kFineLutCells uint4 entries).
 constexpr int kFineLutShift = 42;
 constexpr uint32_t kFineLutCells = (uint32_t)((kEncTop - 1) >> kFineLutShift) + 2;
+constexpr uint32_t kLutL1Words = 4;    // words of a level-1 entry
 constexpr uint32_t kLutDense = 4;      // cells with more splitters get a level-2 split
 constexpr uint32_t kLutMaxBits = 14;   // at most 2^14 sub-cells per cell
 constexpr uint32_t kLutOversplit = 2;  // sub-cells = 4 x the cell's splitters rounded up to a power of two
@@ -126,21 +129,27 @@ inline size_t lut_level2_words(uint32_t log2B) {
   return 8 * B + B / 4 + 256;
 }
 // words of the whole index (level 1 and level 2)
-inline size_t lut_words_for(uint32_t log2B) { return 2 * (size_t)kFineLutCells + lut_level2_words(log2B); }
+inline size_t lut_words_for(uint32_t log2B) {
+  return kLutL1Words * (size_t)kFineLutCells + lut_level2_words(log2B);
+}
 
-// [lo, hi]: the search range of splitter indices for x
+// [lo, hi]: the search range of splitter indices for x (lo == hi: resolved)
 __device__ __forceinline__ void lut_range(const uint32_t* __restrict__ lut, uint64_t x, uint32_t& lo, uint32_t& hi) {
-  const uint2* l1 = reinterpret_cast<const uint2*>(lut);
+  const uint4* l1 = reinterpret_cast<const uint4*>(lut);
   const uint32_t c = (uint32_t)(x >> kFineLutShift);
-  const uint2 a = __ldg(l1 + c), b = __ldg(l1 + c + 1);
+  const uint4 a = __ldg(l1 + c);
   lo = a.x;
-  hi = b.x;
+  hi = __ldg(lut + kLutL1Words * (c + 1));  // the next cell's .x
   if (a.y) {
     const uint32_t nb = a.y & 31, off = a.y >> 5;
     const uint32_t k = (uint32_t)(x >> (kFineLutShift - nb)) & ((1u << nb) - 1);
-    const uint32_t* l2 = lut + 2 * kFineLutCells + off;
+    const uint32_t* l2 = lut + kLutL1Words * kFineLutCells + off;
     lo = __ldg(l2 + k);
     hi = __ldg(l2 + k + 1);
+  } else if (hi == lo + 1) {  // one splitter in the cell: its value is in the entry
+    const uint64_t next = ((uint64_t)a.w << 32) | a.z;
+    lo = next <= x ? hi : lo;
+    hi = lo;
   }
 }
 

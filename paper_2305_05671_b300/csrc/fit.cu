@@ -482,13 +482,15 @@ __global__ void splitter_batch_kernel(const DNode* __restrict__ nodes, uint32_t 
 }
 
 // radix index of the splitters, level 1: cells c with t[q] <= c << 42 < t[q+1] hold q
-__global__ void fine_lut_kernel(const uint64_t* __restrict__ t, uint32_t log2B, uint2* __restrict__ lut) {
+__global__ void fine_lut_kernel(const uint64_t* __restrict__ t, uint32_t log2B, uint4* __restrict__ lut) {
   const uint32_t B = 1u << log2B;
   const uint64_t cell = 1ull << kFineLutShift;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < B; q += gridDim.x * blockDim.x) {
     const uint64_t c0 = (t[q] + cell - 1) >> kFineLutShift;
     const uint64_t c1 = q + 1 < B ? (t[q + 1] + cell - 1) >> kFineLutShift : (uint64_t)kFineLutCells;
-    for (uint64_t c = c0; c < c1 && c < kFineLutCells; ++c) lut[c] = make_uint2(q, 0u);
+    const uint64_t next = q + 1 < B ? t[q + 1] : kEncTop;  // above every key past the last splitter
+    for (uint64_t c = c0; c < c1 && c < kFineLutCells; ++c)
+      lut[c] = make_uint4(q, 0u, (uint32_t)next, (uint32_t)(next >> 32));
   }
 }
 
@@ -500,7 +502,7 @@ __device__ __forceinline__ uint32_t lut_split_bits(uint32_t cnt) {
 }
 
 // level-2 sizes (2^nb + 1 per dense cell): per block of 1024 cells, their total
-__device__ __forceinline__ uint32_t lut_cell_bits(const uint2* lut, uint32_t c) {
+__device__ __forceinline__ uint32_t lut_cell_bits(const uint4* lut, uint32_t c) {
   return c + 1 < kFineLutCells ? lut_split_bits(lut[c + 1].x - lut[c].x) : 0u;
 }
 __device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t* wsum) {
@@ -512,7 +514,7 @@ __device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t* wsum) {
   for (int w = 0; w < 32; ++w) t += wsum[w];
   return t;
 }
-__global__ void __launch_bounds__(1024) lut_block_sizes_kernel(const uint2* __restrict__ lut, uint32_t* __restrict__ part) {
+__global__ void __launch_bounds__(1024) lut_block_sizes_kernel(const uint4* __restrict__ lut, uint32_t* __restrict__ part) {
   __shared__ uint32_t wsum[32];
   const uint32_t c = blockIdx.x * 1024 + threadIdx.x;
   const uint32_t nb = c < kFineLutCells ? lut_cell_bits(lut, c) : 0;
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(1024) lut_block_sizes_kernel(const uint2* __re
 
 // level-2 offsets: exclusive scan of the sizes (block carry from the block
 // totals before it), written into the cells' .y as (offset << 5) | nb
-__global__ void __launch_bounds__(1024) lut_offsets_kernel(uint2* __restrict__ lut, const uint32_t* __restrict__ part) {
+__global__ void __launch_bounds__(1024) lut_offsets_kernel(uint4* __restrict__ lut, const uint32_t* __restrict__ part) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t carry_sh;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -559,11 +561,11 @@ __global__ void __launch_bounds__(1024) lut_offsets_kernel(uint2* __restrict__ l
 
 // level-2 entries: a warp per dense cell, lanes over its sub-cell starts;
 // entry k = largest q in the cell's range with t[q] <= the sub-cell's start
-__global__ void lut_fill_kernel(const uint64_t* __restrict__ t, const uint2* __restrict__ lut, uint32_t* __restrict__ l2) {
+__global__ void lut_fill_kernel(const uint64_t* __restrict__ t, const uint4* __restrict__ lut, uint32_t* __restrict__ l2) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (blockDim.x >> 5);
   for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c + 1 < kFineLutCells; c += warps) {
-    const uint2 a = lut[c];
+    const uint4 a = lut[c];
     if (!a.y) continue;
     const uint32_t nb = a.y & 31, off = a.y >> 5;
     const uint32_t q0 = a.x, q1 = lut[c + 1].x;
@@ -633,14 +635,15 @@ cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t
 
 cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* lut, cudaStream_t st) {
   const uint32_t B = 1u << log2B;
-  uint2* l1 = reinterpret_cast<uint2*>(lut);
+  uint4* l1 = reinterpret_cast<uint4*>(lut);
+  uint32_t* l2 = lut + kLutL1Words * kFineLutCells;
   fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, log2B, l1);
   const uint32_t blocks = (kFineLutCells + 1023) / 1024;
   // block totals go to the last 256 words of level 2, which the entries never reach
-  uint32_t* part = lut + 2 * kFineLutCells + lut_level2_words(log2B) - 256;
+  uint32_t* part = l2 + lut_level2_words(log2B) - 256;
   lut_block_sizes_kernel<<<blocks, 1024, 0, st>>>(l1, part);
   lut_offsets_kernel<<<blocks, 1024, 0, st>>>(l1, part);
-  lut_fill_kernel<<<(kFineLutCells + 7) / 8, 256, 0, st>>>(splitters, l1, lut + 2 * kFineLutCells);
+  lut_fill_kernel<<<(kFineLutCells + 7) / 8, 256, 0, st>>>(splitters, l1, l2);
   return cudaGetLastError();
 }
 
