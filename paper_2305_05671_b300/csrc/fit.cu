@@ -437,15 +437,51 @@ __device__ __forceinline__ uint32_t tree_bin(const DNode* __restrict__ nodes, ui
 }
 
 // fine-bin splitters: t[q] = smallest encoding whose bin is >= q (t[0] = 0);
-// 95^9 when no key reaches bin q
-__global__ void splitter_kernel(const DNode* __restrict__ nodes, uint32_t log2B, uint64_t* t) {
+// 95^9 when no key reaches bin q.  The bin is a monotone function of the
+// encoding, so a bisection over any bracket [lo, hi] holding the answer gives
+// the same t[q] as one over the whole range; the bracket comes from the
+// sorted sample xs (the model was fitted to its ranks, so the bin of xs[k] is
+// near B k / S): start at k = q S / B and gallop outwards to a sample key on
+// each side of the answer, then bisect between them.
+__global__ void splitter_kernel(const DNode* __restrict__ nodes, uint32_t log2B, uint64_t* t,
+                                const uint64_t* __restrict__ xs, uint64_t S) {
   const uint32_t B = 1u << log2B;
   for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < B; q += gridDim.x * blockDim.x) {
     if (q == 0) {
       t[0] = 0;
       continue;
     }
-    uint64_t lo = 0, hi = kEncTop;
+    uint64_t lo = 0, hi = kEncTop;  // the answer lies in [lo, hi]
+    if (S) {
+      uint64_t k = ((uint64_t)q * S) >> log2B;  // q < 2^20, S < 2^24: no overflow
+      if (k > S - 1) k = S - 1;
+      if (tree_bin(nodes, 0, xs[k], log2B) >= q) {  // answer <= xs[k]: walk down to a key below it
+        hi = xs[k];
+        for (uint64_t step = 1;; step <<= 1) {
+          if (k == 0) break;  // lo stays 0
+          const uint64_t i = k > step ? k - step : 0;
+          if (tree_bin(nodes, 0, xs[i], log2B) >= q) {
+            hi = xs[i];
+            k = i;
+          } else {
+            lo = xs[i] + 1;
+            break;
+          }
+        }
+      } else {  // answer > xs[k]: walk up to a key at or above it
+        lo = xs[k] + 1;
+        for (uint64_t step = 1;; step <<= 1) {
+          if (k == S - 1) break;  // hi stays 95^9
+          const uint64_t i = k + step < S - 1 ? k + step : S - 1;
+          if (tree_bin(nodes, 0, xs[i], log2B) >= q) {
+            hi = xs[i];
+            break;
+          }
+          lo = xs[i] + 1;
+          k = i;
+        }
+      }
+    }
     while (lo < hi) {
       uint64_t mid = lo + ((hi - lo) >> 1);
       if (tree_bin(nodes, 0, mid, log2B) >= q) hi = mid;
@@ -765,7 +801,7 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sort
   h.levels = levels;
   // 4. splitters of the fine bins
   const uint32_t B = 1u << a.log2B;
-  splitter_kernel<<<(B + 127) / 128, 128, 0, st>>>(nodes, a.log2B, splitters);
+  splitter_kernel<<<(B + 127) / 128, 128, 0, st>>>(nodes, a.log2B, splitters, x, S);
   build_fine_lut(splitters, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut), st);
   write_header<<<1, 1, 0, st>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
   L += 3;
