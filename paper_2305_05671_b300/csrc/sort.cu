@@ -2,10 +2,11 @@
 // touch-up of Sec. 4) on the GPU.  A work item is a run of consecutive fine
 // bins (model sub-buckets) of one partition holding at most `cap` pairs.  One
 // CTA sorts an item in shared memory -- a counting sort on the leading bits of
-// the keys' base-95 encoding below the item's common prefix (a placement by
-// value, like the model's), long runs refined the same way by warps on their
-// own key range, short runs finished by insertion sort (the touch-up) -- and
-// gathers the 100-byte records of the item, in order, straight into their
+// the keys' base-95 encoding over the item's key range (a placement by value,
+// like the model's), every bucket of up to kRankMax pairs then finished by
+// ranking each pair against its bucket (the touch-up, one thread per pair),
+// longer buckets split again the same way by warps on their own key range --
+// and gathers the 100-byte records of the item, in order, straight into their
 // final place in the output, so the partitions come out concatenated with no
 // merge.  Items above `cap` pairs (heavy duplicate keys) take a multi-pass
 // path: chunk sorts plus merge passes through global memory.
