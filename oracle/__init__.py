@@ -59,6 +59,12 @@ def lib():
             "eo_mlp_forward64": (None, [P, P, U64, P]),
             "eo_mlp_grad64": (None, [P, P, P, U64, P]),
             "eo_mlp_train64": (None, [P, P, P, U64, U32, U32, ctypes.c_double, P]),
+            "eo_mlp_adam64": (None, [P, P, P, P, U64, ctypes.c_double]),
+            "eo_radix_bins": (None, [P, U64, U32, P]),
+            "eo_radix_splitters": (None, [U32, P]),
+            "eo_sort_by_splitters": (I32, [P, U64, P, U32, U32, I32, P, P, P, P, P, P]),
+            "eo_model_choice": (I32, [P, U64, U32, U32, U32, U32, U64, U64, I32, P, U32, P]),
+            "eo_sort_threads": (I32, [P, U64, U32, U32, U32, U32, U64, U64, I32, P, U32]),
             "eo_mlp_splitters": (None, [P, P, U32, P]),
             "eo_bins_by_splitters": (None, [P, U32, P, U64, P]),
             "eo_validate": (I32, [P, P, U64]),
@@ -272,3 +278,71 @@ def bins_by_splitters(t: np.ndarray, log2B: int, xs: np.ndarray) -> np.ndarray:
     q = np.empty(xs.size, dtype=np.uint32)
     lib().eo_bins_by_splitters(_ptr(np.ascontiguousarray(t, dtype=np.uint64)), log2B, _ptr(xs), xs.size, _ptr(q))
     return q
+
+
+def mlp_adam64(w, g, m, v, t: int, lr: float = 1e-3):
+    """One Adam step (FP64) at step number t from state (m, v); returns new (w, m, v)."""
+    w = np.array(w, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    m = np.array(m, dtype=np.float64)
+    v = np.array(v, dtype=np.float64)
+    lib().eo_mlp_adam64(_ptr(w), _ptr(g), _ptr(m), _ptr(v), t, lr)
+    return w, m, v
+
+
+# ---------------------------------------------------------------- radix partitioning, classifiers by splitters
+def radix_bins(xs: np.ndarray, log2B: int) -> np.ndarray:
+    xs = np.ascontiguousarray(xs, dtype=np.uint64)
+    q = np.empty(xs.size, dtype=np.uint32)
+    lib().eo_radix_bins(_ptr(xs), xs.size, log2B, _ptr(q))
+    return q
+
+
+def radix_splitters(log2B: int) -> np.ndarray:
+    t = np.empty(1 << log2B, dtype=np.uint64)
+    lib().eo_radix_splitters(log2B, _ptr(t))
+    return t
+
+
+def sort_by_splitters(recs: np.ndarray, t: np.ndarray, log2B: int, P: int, balance: int = 1, want_out: bool = True):
+    """The method with a given classifier (splitters t): (out or None, detail dict)."""
+    n = recs.size // RECORD
+    B = 1 << log2B
+    t = np.ascontiguousarray(t, dtype=np.uint64)
+    out = np.empty_like(recs) if want_out else None
+    q = np.empty(n, dtype=np.uint32)
+    pid = np.empty(n, dtype=np.uint32)
+    off = np.empty(P + 1, dtype=np.uint64)
+    counts = np.empty(B, dtype=np.uint64)
+    cuts = np.empty(P + 1, dtype=np.uint32)
+    rc = lib().eo_sort_by_splitters(_ptr(recs), n, _ptr(t), log2B, P, balance, _ptr(out), _ptr(q), _ptr(pid),
+                                    _ptr(off), _ptr(counts), _ptr(cuts))
+    if rc:
+        raise ValueError(f"eo_sort_by_splitters rc={rc}")
+    return out, dict(q=q, pid=pid, part_off=off, bin_counts=counts, cuts=cuts)
+
+
+MODEL_CHOICE_DIAG = ("rmi_max_bucket", "mlp_max_bucket", "J", "F_first_knot", "F_last_knot", "mlp_max_partition")
+
+
+def model_choice(recs: np.ndarray, P: int, log2B: int, S: int, seed: int, balance: int, w: np.ndarray,
+                 skip: int = 0, T: int = LEAF_TARGET, Dmax: int = MAX_DEPTH):
+    """The network-or-RMI decision for given network weights: (reason, diagnostics dict)."""
+    n = recs.size // RECORD
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    diag = np.zeros(6)
+    r = int(lib().eo_model_choice(_ptr(recs), n, P, log2B, T, Dmax, S, seed, balance, _ptr(w), skip, _ptr(diag)))
+    if r < 0:
+        raise ValueError("eo_model_choice rejected its arguments")
+    return r, dict(zip(MODEL_CHOICE_DIAG, diag.tolist()))
+
+
+def sort_threads(recs: np.ndarray, P: int, log2B: int, S: int, seed: int, balance: int = 1, threads: int = 1,
+                 T: int = LEAF_TARGET, Dmax: int = MAX_DEPTH) -> np.ndarray:
+    """eo_sort over `threads` host threads (classification ranges, partitions sorted in parallel)."""
+    n = recs.size // RECORD
+    out = np.empty_like(recs)
+    rc = lib().eo_sort_threads(_ptr(recs), n, P, log2B, T, Dmax, S, seed, balance, _ptr(out), threads)
+    if rc:
+        raise ValueError(f"eo_sort_threads rc={rc}")
+    return out

@@ -19,14 +19,20 @@
 //   sort      Sec. 3.4 / Sec. 4 touch-up: each partition in key byte order
 //             (memcmp), ties kept in input order
 //   concat    Sec. 3.5: partitions written back to back, no merge
+// Beside the method: the radix classifier the paper compares it with (Sec. 3,
+// Sec. 3.3), the method with any given classifier (splitters), the choice
+// between the learned network and the RMI, and the paper's multi-threaded
+// CPU form (Sec. 5) for timing on all host cores.
 // Readings of places the paper leaves open are listed beside each function.
 //
 // Parity of this oracle is pinned by tests/test_oracle_*.py (closed forms,
 // brute force, invariants, library least squares); see those files.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 namespace {
@@ -289,6 +295,44 @@ void stable_sort_indices(const uint8_t* recs, std::vector<uint64_t>& idx) {
   std::stable_sort(idx.begin(), idx.end(), [recs](uint64_t a, uint64_t b) { return key_less(recs, a, b); });
 }
 
+// Sec. 3.3 - 3.5 given the fine bin q of every record: cuts, partition lists
+// in input order, a stable sort of each by memcmp, concatenation.  Optional
+// outputs as eo_sort's.
+void partition_sort_concat(const uint8_t* in, uint64_t n, const std::vector<uint32_t>& q,
+                           const std::vector<uint64_t>& counts, uint32_t P, uint32_t log2B, int balance, uint8_t* out,
+                           uint32_t* q_out, uint32_t* pid_out, uint64_t* part_off, uint64_t* bin_counts,
+                           uint32_t* cuts_out) {
+  const uint32_t B = 1u << log2B;
+  std::vector<uint32_t> c = cuts_of(counts, P, log2B, n, balance);
+  std::vector<uint32_t> pid_of_bin(B);
+  for (uint32_t t = 0; t < B; ++t) pid_of_bin[t] = pid_of(c, P, t);
+  std::vector<std::vector<uint64_t>> part(P);
+  for (uint64_t i = 0; i < n; ++i) part[pid_of_bin[q[i]]].push_back(i);
+  uint64_t off = 0;
+  for (uint32_t p = 0; p < P; ++p) {
+    if (part_off) part_off[p] = off;
+    stable_sort_indices(in, part[p]);
+    for (uint64_t i : part[p]) {
+      if (out) std::memcpy(out + off * kRecord, in + i * kRecord, kRecord);
+      ++off;
+    }
+  }
+  if (part_off) part_off[P] = off;
+  for (uint64_t i = 0; i < n; ++i) {
+    if (q_out) q_out[i] = q[i];
+    if (pid_out) pid_out[i] = pid_of_bin[q[i]];
+  }
+  if (bin_counts)
+    for (uint32_t t = 0; t < B; ++t) bin_counts[t] = counts[t];
+  if (cuts_out)
+    for (uint32_t p = 0; p <= P; ++p) cuts_out[p] = c[p];
+}
+
+// fine bin by splitters t[0..B): the number of q >= 1 with t[q] <= x
+inline uint32_t bin_by_splitters(const uint64_t* t, uint32_t B, uint64_t x) {
+  return (uint32_t)(std::upper_bound(t + 1, t + B, x) - (t + 1));
+}
+
 uint64_t parse_index(const uint8_t* rec, bool* ok) {
   uint64_t v = 0;
   *ok = true;
@@ -400,29 +444,7 @@ int eo_sort(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint32_t 
     q[i] = fine_bin(rmi_cdf(m, encode9(in + i * kRecord)), log2B);
     counts[q[i]]++;
   }
-  std::vector<uint32_t> c = cuts_of(counts, P, log2B, n, balance);
-  std::vector<uint32_t> pid_of_bin(B);
-  for (uint32_t t = 0; t < B; ++t) pid_of_bin[t] = pid_of(c, P, t);
-  std::vector<std::vector<uint64_t>> part(P);
-  for (uint64_t i = 0; i < n; ++i) part[pid_of_bin[q[i]]].push_back(i);
-  uint64_t off = 0;
-  for (uint32_t p = 0; p < P; ++p) {
-    if (part_off) part_off[p] = off;
-    stable_sort_indices(in, part[p]);
-    for (uint64_t i : part[p]) {
-      std::memcpy(out + off * kRecord, in + i * kRecord, kRecord);
-      ++off;
-    }
-  }
-  if (part_off) part_off[P] = off;
-  for (uint64_t i = 0; i < n; ++i) {
-    if (q_out) q_out[i] = q[i];
-    if (pid_out) pid_out[i] = pid_of_bin[q[i]];
-  }
-  if (bin_counts)
-    for (uint32_t t = 0; t < B; ++t) bin_counts[t] = counts[t];
-  if (cuts_out)
-    for (uint32_t p = 0; p <= P; ++p) cuts_out[p] = c[p];
+  partition_sort_concat(in, n, q, counts, P, log2B, balance, out, q_out, pid_out, part_off, bin_counts, cuts_out);
   return 0;
 }
 
@@ -481,6 +503,184 @@ int eo_validate(const uint8_t* in, const uint8_t* out, uint64_t n) {
     prev_idx = idx;
   }
   return bad;
+}
+
+// ---------------------------------------------------------------- radix partitioning (Sec. 3, Sec. 3.3)
+// The paper compares its model-based partitions with radix-based ones, which
+// give every partition an equal range of the key domain whatever the data
+// (sensitive to skew).  Reading taken here: equal-width ranges of the
+// printable key domain, i.e. fine bin q = floor(x * B / 95^9) of the key
+// encoding x -- the most significant base-95 digits when B is a power of 95,
+// equal slices of the same domain for B a power of two.  Exact in 128 bits.
+// Its splitters (the smallest encoding of bin >= q) are ceil(q * 95^9 / B).
+void eo_radix_bins(const uint64_t* xs, uint64_t n, uint32_t log2B, uint32_t* q) {
+  const u128 top = (u128)630249409724609375ull;  // 95^9
+  for (uint64_t i = 0; i < n; ++i) q[i] = (uint32_t)(((u128)xs[i] << log2B) / top);
+}
+
+void eo_radix_splitters(uint32_t log2B, uint64_t* t) {
+  const u128 top = (u128)630249409724609375ull;
+  const uint64_t B = 1ull << log2B;
+  for (uint64_t q = 0; q < B; ++q) t[q] = (uint64_t)(((u128)q * top + (B - 1)) >> log2B);
+}
+
+// Sec. 3.3 - 3.5 with a given classifier: the fine bin of record i is the
+// number of splitters t[1..B) at or below its key encoding (t non-decreasing,
+// t[0] = 0); then counts, cuts (paper or refined rule), partitions stably
+// sorted and concatenated.  `out` may be null (classification only).
+int eo_sort_by_splitters(const uint8_t* in, uint64_t n, const uint64_t* t, uint32_t log2B, uint32_t P, int balance,
+                         uint8_t* out, uint32_t* q_out, uint32_t* pid_out, uint64_t* part_off, uint64_t* bin_counts,
+                         uint32_t* cuts_out) {
+  if (P < 1 || (P & (P - 1)) || log2B > 24 || (1u << log2B) < P) return 1;
+  const uint32_t B = 1u << log2B;
+  for (uint32_t k = 1; k < B; ++k)
+    if (t[k] < t[k - 1]) return 1;
+  std::vector<uint32_t> q(n);
+  std::vector<uint64_t> counts(B, 0);
+  for (uint64_t i = 0; i < n; ++i) {
+    q[i] = bin_by_splitters(t, B, encode9(in + i * kRecord));
+    counts[q[i]]++;
+  }
+  partition_sort_concat(in, n, q, counts, P, log2B, balance, out, q_out, pid_out, part_off, bin_counts, cuts_out);
+  return 0;
+}
+
+// ---------------------------------------------------------------- the model choice
+// The learned network is an addition of this project (the paper's model is
+// the RMI); the RMI stays its fallback and judges it.  Given the network's
+// weights w (1505 FP32, layout of mlp_oracle.cpp), the rule is:
+//   knots   from the sorted sample (seed), as the network was trained on it;
+//   check 1 (boundary)  F(T_0) < 1/16 and F(T_12) > 15/16 in FP32, else reason 1;
+//   check 2 (judge)     a held-out sample (seed + 1, S keys) put into J judge
+//                       buckets (groups of 2^(log2B - log2J) consecutive fine
+//                       bins; log2J the largest value <= log2B, at least 1, with
+//                       64 * 2^log2J <= S) by the RMI's fine bins and by the
+//                       network's splitters: the network's largest bucket may
+//                       not hold more keys than the RMI's, else reason 2;
+//   check 3 (full data) the network's partitions of all n records (its
+//                       splitters, the configured cut rule): the largest may
+//                       not exceed 1.1 times the mean, else reason 3.
+// skip bit k-1 skips check k.  Returns the reason (0 = the network is used),
+// or -1 on bad input.  diag (nullable, 6 doubles): largest RMI bucket,
+// largest network bucket, J, F(T_0), F(T_12), largest network partition
+// (0 when check 3 did not run).
+extern "C" void eo_mlp_knots(const uint64_t* sorted, uint64_t S, uint64_t* T);
+extern "C" void eo_mlp_features(const uint64_t* T, const uint64_t* xs, uint64_t n, float* phi);
+extern "C" void eo_mlp_forward32(const float* w, const float* phi, uint64_t n, float* F);
+extern "C" void eo_mlp_splitters(const float* w, const uint64_t* T, uint32_t log2B, uint64_t* t);
+
+int eo_model_choice(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint32_t T, uint32_t Dmax, uint64_t S,
+                    uint64_t seed, int balance, const float* w, uint32_t skip, double* diag) {
+  if (n == 0 || S == 0 || S >= (1ull << 24) || log2B < 1 || log2B > 22 || (1u << log2B) < P || P < 1 ||
+      (P & (P - 1)) || T < 1)
+    return -1;
+  const uint32_t B = 1u << log2B;
+  std::vector<uint64_t> sample(S), held(S);
+  eo_sample(in, n, S, seed, sample.data());
+  std::sort(sample.begin(), sample.end());
+  Rmi m = rmi_fit(sample.data(), S, T, Dmax);
+  uint64_t knots[13];
+  eo_mlp_knots(sample.data(), S, knots);
+  std::vector<uint64_t> t(B);
+  eo_mlp_splitters(w, knots, log2B, t.data());
+  // check 1: F at the first and last knot
+  float phi[2 * 12], Fk[2];
+  const uint64_t ends[2] = {knots[0], knots[12]};
+  eo_mlp_features(knots, ends, 2, phi);
+  eo_mlp_forward32(w, phi, 2, Fk);
+  // check 2: the held-out judge
+  uint32_t log2J = 1;
+  while (log2J < log2B && (64ull << (log2J + 1)) <= S) ++log2J;
+  const uint32_t J = 1u << log2J;
+  eo_sample(in, n, S, seed + 1, held.data());
+  std::vector<uint64_t> hr(J, 0), hm(J, 0);
+  for (uint64_t k = 0; k < S; ++k) {
+    hr[fine_bin(rmi_cdf(m, held[k]), log2B) >> (log2B - log2J)]++;
+    hm[bin_by_splitters(t.data(), B, held[k]) >> (log2B - log2J)]++;
+  }
+  const uint64_t mr = *std::max_element(hr.begin(), hr.end()), mm = *std::max_element(hm.begin(), hm.end());
+  int reason = 0;
+  if (!(skip & 1) && !(Fk[0] < 1.0f / 16 && Fk[1] > 1.0f - 1.0f / 16)) reason = 1;
+  else if (!(skip & 2) && mm > mr) reason = 2;
+  uint64_t maxpart = 0;
+  if (reason == 0 && !(skip & 4)) {
+    std::vector<uint64_t> off(P + 1);
+    eo_sort_by_splitters(in, n, t.data(), log2B, P, balance, nullptr, nullptr, nullptr, off.data(), nullptr, nullptr);
+    for (uint32_t p = 0; p < P; ++p) maxpart = std::max<uint64_t>(maxpart, off[p + 1] - off[p]);
+    if ((double)maxpart * P > 1.1 * (double)n) reason = 3;
+  }
+  if (diag) {
+    diag[0] = (double)mr;
+    diag[1] = (double)mm;
+    diag[2] = (double)J;
+    diag[3] = Fk[0];
+    diag[4] = Fk[1];
+    diag[5] = (double)maxpart;
+  }
+  return reason;
+}
+
+// ---------------------------------------------------------------- the paper's CPU design, threaded
+// eo_sort with the work spread over `threads` host threads the way the paper's
+// CPU implementation spreads it (Sec. 5): the records are classified in
+// contiguous ranges by all threads, and the partitions are sorted in parallel,
+// each thread taking the next unsorted partition (dynamic scheduling).  The
+// result is eo_sort's exactly: the classification and cuts are the same
+// function, the partition lists keep input order, and each partition is
+// sorted stably on its own.  Used to time the oracle on all host cores.
+int eo_sort_threads(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint32_t T, uint32_t Dmax, uint64_t S,
+                    uint64_t seed, int balance, uint8_t* out, uint32_t threads) {
+  if (P < 1 || (P & (P - 1)) || log2B > 24 || (1u << log2B) < P || T < 1 || threads < 1) return 1;
+  if (S >= (1ull << 24) || (n > 0 && S == 0)) return 1;
+  if (n == 0) return 0;
+  std::vector<uint64_t> sample(S);
+  eo_sample(in, n, S, seed, sample.data());
+  std::sort(sample.begin(), sample.end());
+  Rmi m = rmi_fit(sample.data(), S, T, Dmax);
+  const uint32_t B = 1u << log2B;
+  std::vector<uint32_t> q(n);
+  std::vector<std::vector<uint64_t>> cnt(threads, std::vector<uint64_t>(B, 0));
+  auto ranges = [&](uint32_t k, uint64_t* a, uint64_t* b) {
+    *a = n * k / threads;
+    *b = n * (k + 1) / threads;
+  };
+  {
+    std::vector<std::thread> pool;
+    for (uint32_t k = 0; k < threads; ++k)
+      pool.emplace_back([&, k]() {
+        uint64_t a, b;
+        ranges(k, &a, &b);
+        for (uint64_t i = a; i < b; ++i) {
+          q[i] = fine_bin(rmi_cdf(m, encode9(in + i * kRecord)), log2B);
+          cnt[k][q[i]]++;
+        }
+      });
+    for (auto& th : pool) th.join();
+  }
+  std::vector<uint64_t> counts(B, 0);
+  for (uint32_t k = 0; k < threads; ++k)
+    for (uint32_t b = 0; b < B; ++b) counts[b] += cnt[k][b];
+  std::vector<uint32_t> c = cuts_of(counts, P, log2B, n, balance);
+  std::vector<uint32_t> pid_of_bin(B);
+  for (uint32_t t = 0; t < B; ++t) pid_of_bin[t] = pid_of(c, P, t);
+  std::vector<std::vector<uint64_t>> part(P);
+  for (uint64_t i = 0; i < n; ++i) part[pid_of_bin[q[i]]].push_back(i);
+  std::vector<uint64_t> off(P + 1, 0);
+  for (uint32_t p = 0; p < P; ++p) off[p + 1] = off[p] + part[p].size();
+  std::atomic<uint32_t> next(0);
+  {
+    std::vector<std::thread> pool;
+    for (uint32_t k = 0; k < threads; ++k)
+      pool.emplace_back([&]() {
+        for (uint32_t p = next++; p < P; p = next++) {
+          stable_sort_indices(in, part[p]);
+          uint64_t o = off[p];
+          for (uint64_t i : part[p]) std::memcpy(out + (o++) * kRecord, in + i * kRecord, kRecord);
+        }
+      });
+    for (auto& th : pool) th.join();
+  }
+  return 0;
 }
 
 }  // extern "C"

@@ -21,9 +21,12 @@
 //           (lr 1e-3, beta 0.9 / 0.999, eps 1e-8), weights projected to >= 0
 //           after every step.
 // Parity: FP64 forward/backward pinned by closed forms and central finite
-// differences (tests/test_oracle_mlp.py).  The GPU trains in FP32, so trained
-// weights are not compared bit for bit; the FP32 forward and the splitters are
-// compared exactly for given weights.
+// differences, the Adam step by its closed forms (first step, constant and
+// alternating gradients, projection of weights only), the splitters by the
+// exact bracket bin(t_q) >= q > bin(t_q - 1) (tests/test_oracle_mlp.py).  The
+// GPU trains in FP32, so trained weights are not compared bit for bit; the
+// FP32 forward and the splitters are compared exactly for given weights, and
+// one Adam step within FP32 rounding.
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -222,12 +225,28 @@ void eo_mlp_grad64(const double* w, const double* phi, const double* y, uint64_t
   for (int i = 0; i < kParams; ++i) g[i] /= (double)n;
 }
 
+// One step of Adam (Kingma & Ba 2015, Algorithm 1) at step number t >= 1 on
+// the gradient g: the moment estimates m, v are updated in place, corrected
+// for their zero start (divided by 1 - beta^t), and every parameter moves by
+// lr * mhat / (sqrt(vhat) + eps); then the weights (not the biases) are
+// projected back onto >= 0, which keeps the network monotone.
+void eo_mlp_adam64(double* w, const double* g, double* m, double* v, uint64_t t, double lr) {
+  const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
+  for (int i = 0; i < kParams; ++i) {
+    m[i] = b1 * m[i] + (1 - b1) * g[i];
+    v[i] = b2 * v[i] + (1 - b2) * g[i] * g[i];
+    double mh = m[i] / (1 - std::pow(b1, (double)t));
+    double vh = v[i] / (1 - std::pow(b2, (double)t));
+    w[i] -= lr * mh / (std::sqrt(vh) + eps);
+    if (is_weight(i) && w[i] < 0.0) w[i] = 0.0;
+  }
+}
+
 // FP64 training (Adam + projection) on features/labels; minibatch b holds
 // samples b, b + nb, b + 2 nb, ... (nb = ceil(n / batch)); w in/out.
 void eo_mlp_train64(double* w, const double* phi, const double* y, uint64_t n, uint32_t batch, uint32_t epochs,
                     double lr, double* loss_out) {
   std::vector<double> mom(kParams, 0.0), vel(kParams, 0.0), g(kParams);
-  const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
   uint64_t nb = (n + batch - 1) / batch;
   uint64_t t = 0;
   Acts a;
@@ -239,16 +258,8 @@ void eo_mlp_train64(double* w, const double* phi, const double* y, uint64_t n, u
         forward64(w, phi + s * kF, a);
         backward64(w, phi + s * kF, y[s], a, g.data());
       }
-      ++t;
-      for (int i = 0; i < kParams; ++i) {
-        double gi = g[i] / (double)cnt;
-        mom[i] = b1 * mom[i] + (1 - b1) * gi;
-        vel[i] = b2 * vel[i] + (1 - b2) * gi * gi;
-        double mh = mom[i] / (1 - std::pow(b1, (double)t));
-        double vh = vel[i] / (1 - std::pow(b2, (double)t));
-        w[i] -= lr * mh / (std::sqrt(vh) + eps);
-        if (is_weight(i) && w[i] < 0.0) w[i] = 0.0;
-      }
+      for (int i = 0; i < kParams; ++i) g[i] /= (double)cnt;
+      eo_mlp_adam64(w, g.data(), mom.data(), vel.data(), ++t, lr);
     }
   }
   if (loss_out) {

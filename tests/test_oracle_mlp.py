@@ -137,3 +137,116 @@ def test_splitters_reproduce_the_fp32_bins(orc):
     direct = np.minimum(255, np.floor(orc.mlp_forward32(w, orc.mlp_features(T, probe)) * 256)).astype(np.uint32)
     assert np.mean(q == direct) > 0.999
     assert np.all(np.diff(q.astype(np.int64)) >= 0)
+
+
+# ---------------------------------------------------------------- Adam (Kingma & Ba 2015, Algorithm 1)
+W_SLICES = ("W1", "W2", "w3")
+B_SLICES = ("b1", "b2", "b3")
+LR = 1e-3
+
+
+def _mask(orc, names):
+    m = np.zeros(1505, bool)
+    for k in names:
+        a, b = orc.MLP_SLICES[k]
+        m[a:b] = True
+    return m
+
+
+def test_adam_first_step_moves_each_parameter_by_lr(orc):
+    """From a zero moment state the bias corrections make mhat = g and
+    vhat = g^2 exactly, so step 1 moves every parameter by lr * |g| / (|g| + eps)
+    against its gradient -- whatever the sign or size of g."""
+    rng = np.random.default_rng(10)
+    w0 = rng.random(1505) + 1.0  # far from the projection
+    g = rng.normal(0, 1, 1505) * 10.0 ** rng.integers(-4, 3, 1505)
+    w, m, v = orc.mlp_adam64(w0, g, np.zeros(1505), np.zeros(1505), 1, LR)
+    assert np.allclose(w - w0, -LR * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
+    assert np.allclose(m, 0.1 * g, rtol=1e-15) and np.allclose(v, 0.001 * g * g, rtol=1e-15)
+
+
+def test_adam_constant_gradient_keeps_step_lr(orc):
+    """With the same gradient every step, mhat = g and vhat = g^2 at every t
+    (the corrections 1 - beta^t undo the zero start exactly), so every step is
+    lr * g / (|g| + eps): a correction taken at the wrong t changes the step."""
+    rng = np.random.default_rng(11)
+    g = rng.normal(0, 1, 1505)
+    w = rng.random(1505) + 1.0
+    m = np.zeros(1505)
+    v = np.zeros(1505)
+    for t in range(1, 6):
+        w_prev = w
+        w, m, v = orc.mlp_adam64(w, g, m, v, t, LR)
+        assert np.allclose(w - w_prev, -LR * g / (np.abs(g) + 1e-8), rtol=1e-10, atol=0), t
+
+
+def test_adam_alternating_gradient_second_step(orc):
+    """Gradient +1 then -1: m_2 = 0.9 * 0.1 - 0.1 = -0.01 and 1 - 0.9^2 = 0.19,
+    so mhat_2 = -1/19; v_2 = 0.999 * 0.001 + 0.001 = 0.001999 = 1 - 0.999^2, so
+    vhat_2 = 1.  The second step is therefore +lr / 19 / (1 + eps).  (With the
+    two decay rates swapped it would be about +lr / 2000.)"""
+    w0 = np.full(1505, 1.0)
+    w1, m, v = orc.mlp_adam64(w0, np.ones(1505), np.zeros(1505), np.zeros(1505), 1, LR)
+    w2, m, v = orc.mlp_adam64(w1, -np.ones(1505), m, v, 2, LR)
+    assert np.allclose(m, -0.01, rtol=1e-12) and np.allclose(v, 0.001999, rtol=1e-12)
+    assert np.allclose(w2 - w1, LR / 19 / (1 + 1e-8), rtol=1e-10)
+
+
+def test_adam_projects_weights_not_biases(orc):
+    """After the step the weights (W1, W2, w3) are projected onto >= 0, which
+    keeps the network monotone; the biases are free to go negative."""
+    g = np.ones(1505)  # every parameter steps down by lr
+    w, _, _ = orc.mlp_adam64(np.zeros(1505), g, np.zeros(1505), np.zeros(1505), 1, LR)
+    wm, bm = _mask(orc, W_SLICES), _mask(orc, B_SLICES)
+    assert np.all(w[wm] == 0.0)
+    assert np.allclose(w[bm], -LR / (1 + 1e-8), rtol=1e-12)
+    assert wm.sum() + bm.sum() == 1505
+
+
+def test_training_one_full_batch_is_gradient_then_adam(orc):
+    """eo_mlp_train64 with one minibatch of all samples and one epoch is one
+    Adam step on the mean-squared-error gradient (whose chain rule is pinned by
+    finite differences above)."""
+    rng = np.random.default_rng(12)
+    w0 = _w(rng)
+    phi = rng.random((300, 12))
+    y = rng.random(300)
+    w, _ = orc.mlp_train64(w0, phi, y, batch=300, epochs=1, lr=LR)
+    g = orc.mlp_grad64(w0, phi, y)
+    want, _, _ = orc.mlp_adam64(w0, g, np.zeros(1505), np.zeros(1505), 1, LR)
+    assert np.array_equal(w, want)
+
+
+def test_splitters_bracket_the_bins_exactly(orc):
+    """t_q is the smallest key encoding whose FP32 fine bin is >= q: bin(t_q) >= q
+    and bin(t_q - 1) < q for every q whose splitter was not raised to its
+    predecessor by the running maximum; t_q = 95^9 only when no encoding
+    reaches bin q."""
+    rng = np.random.default_rng(13)
+    x = np.sort(rng.integers(0, 95**9, 20001, dtype=np.uint64))
+    T = orc.mlp_knots(x)
+    log2B = 9
+    B = 1 << log2B
+    top = np.uint64(95**9)
+    for seed in range(3):
+        r = np.random.default_rng(100 + seed)
+        w = orc.mlp_init().astype(np.float64)
+        w += np.abs(r.normal(0, 0.05, w.size)) * (np.abs(w) + 0.05)  # non-negative perturbation keeps it monotone
+        w = w.astype(np.float32)
+        t = orc.mlp_splitters(w, T, log2B)
+        assert t[0] == 0 and np.all(np.diff(t.astype(np.float64)) >= 0)
+
+        def fbin(v):
+            F = orc.mlp_forward32(w, orc.mlp_features(T, np.ascontiguousarray(v, dtype=np.uint64)))
+            return np.minimum(B - 1, np.floor(F.astype(np.float64) * B)).astype(np.int64)
+
+        q = np.arange(1, B)
+        tq = t[1:]
+        raised = np.concatenate([[False], tq[1:] == tq[:-1]])
+        inside = (tq < top) & ~raised
+        assert inside.sum() > B // 2
+        assert np.all(fbin(tq[inside]) >= q[inside])
+        pos = inside & (tq > 0)
+        assert np.all(fbin(tq[pos] - np.uint64(1)) < q[pos])
+        # splitters left at 95^9: even the largest encoding stays below bin q
+        assert np.all(fbin(np.array([95**9 - 1], dtype=np.uint64))[0] < q[tq == top])

@@ -146,3 +146,68 @@ def test_single_key_sample(orc):
 def test_unsorted_sample_rejected(orc):
     with pytest.raises(ValueError):
         orc.Rmi(np.array([5, 3], dtype=np.uint64), T)
+
+
+def _budget_sample(S=20000, frac=0.8, A=1000):
+    """A block of equal keys with a geometric tail of larger keys: every level's
+    linear router sends the block (and the tail's smallest keys) to one child,
+    which splits again, so each level adds about S/T nodes until the node
+    budget stops the tree."""
+    nb = int(S * frac)
+    k = np.arange(S - nb)
+    off = np.floor(2.0 ** (58.0 * k / (S - nb - 1))).astype(np.uint64)
+    return np.sort(np.concatenate([np.full(nb, A, dtype=np.uint64), np.uint64(A) + off]))
+
+
+def _route_exact(gamma, delta, scale, fanout, base, shift, x):
+    """The router clamp(floor(fma(gamma, u, delta) * scale), 0, f-1), with the
+    fused multiply-add done in exact rationals and rounded once to double."""
+    from fractions import Fraction
+
+    u = (int(x) - int(base)) >> int(shift) if int(x) > int(base) else 0
+    t = float(Fraction(float(gamma)) * u + Fraction(float(delta))) * float(scale)
+    if not t > 0.0:
+        return 0
+    return fanout - 1 if t >= fanout else int(t)
+
+
+def test_node_budget_caps_a_whole_level(orc):
+    """The budget rule of the RMI reading (Sec. 3.1 defers the architecture to
+    the RMI papers): the children of a level are created only if the tree then
+    holds at most 4*ceil(S/T) + 1024 nodes; otherwise every node of that level
+    becomes a leaf.  Checked on a sample that reaches the budget: every level
+    that split stayed within it, the level that did not split would have gone
+    past it, and that level is all leaves."""
+    x = _budget_sample()
+    S = x.size
+    budget = 4 * (-(-S // T)) + 1024
+    m = orc.Rmi(x, T)
+    assert len(m) <= budget
+    depth = m.depth.astype(np.int64)
+    levels = int(depth.max()) + 1
+    before = 0
+    for d in range(levels):
+        idx = np.nonzero(depth == d)[0]
+        would = 0  # children this level's nodes would create under the split rule alone
+        for i in idx:
+            s, e = int(m.s_[i]), int(m.e_[i])
+            n = e - s
+            if n <= 2 * T or x[s] == x[e - 1] or d >= 32:
+                continue
+            f = -(-n // T)
+            if _route_exact(m.gamma[i], m.delta[i], f / n, f, m.base[i], m.shift[i], x[s]) == \
+                    _route_exact(m.gamma[i], m.delta[i], f / n, f, m.base[i], m.shift[i], x[e - 1]):
+                continue
+            would += f
+        total_after_level = before + len(idx)
+        if d < levels - 1:
+            assert total_after_level + would <= budget
+            assert int(m.fanout[idx].astype(np.int64).sum()) == would  # every node that may split did
+        else:
+            assert would > 0 and total_after_level + would > budget  # the cap is what stopped the tree
+            assert np.all(m.fanout[idx] == 0)  # all of the level, not node by node
+        before = total_after_level
+    assert before == len(m)
+    # the capped level's leaves still clamp to their rank ranges: F stays monotone in [0, 1]
+    F, _ = m.eval(np.sort(np.concatenate([x, x + np.uint64(1)])))
+    assert np.all(np.diff(F) >= 0) and F.min() >= 0 and F.max() <= 1
