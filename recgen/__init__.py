@@ -14,6 +14,11 @@ Definitions (identical in the C and CUDA implementations):
   fixed-point CDF table of ``r^-s`` (built here in FP64, shared as integers),
   then ``0x20 + perm[pos][r]`` with a per-position Fisher-Yates permutation
   drawn from stream 3
+* prefix-skew key (the paper's skewed data, Sec. 7.1: a table of 128 6-byte
+  entries, the key's leading bytes of record i replaced by entry
+  ``log2(i) mod 128``): uniform bytes, then bytes 0-5 replaced by entry
+  ``t = floor(log2 i) mod 128`` (record 0: entry 0) of a seed-drawn table whose
+  byte p of entry t is ``0x20 + mulhi32(h(t,p,4) >> 32, 95)``
 * duplicates: with probability d (``h(i,10,1) < floor(d*2^64)``) the key is the
   base key of record ``mulhi64(h(i,11,1), n)``
 * payload: 32 hex digits of i, 56 filler letters, CRLF
@@ -49,14 +54,14 @@ def h(seed: int, i: int, pos: int, stream: int) -> int:
 class KeySpec:
     """How the 10-byte keys of one record set are drawn."""
 
-    kind: str = "uniform"  # "uniform" | "zipf"
+    kind: str = "uniform"  # "uniform" | "zipf" | "prefix" (the paper's table-of-prefixes skew)
     s: float = 1.1  # Zipf exponent (kind == "zipf")
     dup: float = 0.0  # fraction of exact-duplicate keys
     seed: int = 1
 
     def tables(self):
         """(cum[94] uint64, perm[10*95] uint8, dup_thr) shared by both generators."""
-        if self.kind == "uniform":
+        if self.kind in ("uniform", "prefix"):
             cum = np.full(94, _M64, dtype=np.uint64)
             perm = np.tile(np.arange(95, dtype=np.uint8), 10)
         elif self.kind == "zipf":
@@ -83,7 +88,7 @@ class KeySpec:
 
     @property
     def kind_code(self) -> int:
-        return 0 if self.kind == "uniform" else 1
+        return {"uniform": 0, "zipf": 1, "prefix": 2}[self.kind]
 
 
 _cpu = None
@@ -172,6 +177,7 @@ def build_gpu():
 UNIFORM_1M = dict(name="uniform-1M", n=1_000_000, spec=KeySpec("uniform", seed=1), P=64)
 UNIFORM_100M = dict(name="uniform-100M", n=100_000_000, spec=KeySpec("uniform", seed=2), P=1024)
 ZIPF11_100M = dict(name="zipf1.1-dup5%-100M", n=100_000_000, spec=KeySpec("zipf", s=1.1, dup=0.05, seed=3), P=1024)
+PREFIX_100M = dict(name="prefix-skew-100M", n=100_000_000, spec=KeySpec("prefix", seed=8), P=1024)
 ZIPF13_500M = dict(name="zipf1.3-dup10%-500M", n=500_000_000, spec=KeySpec("zipf", s=1.3, dup=0.10, seed=5),
                    P=4096)
 

@@ -31,7 +31,12 @@ __device__ __forceinline__ uint64_t hrand(uint64_t seed, uint64_t i, uint64_t po
 
 __device__ __forceinline__ uint8_t key_byte(const Spec& s, const uint64_t* cum, const uint8_t* perm,
                                             uint64_t i, int pos) {
-  if (s.kind == 0) {
+  if (s.kind == 2 && pos < 6) {  // prefix skew: entry floor(log2 i) mod 128 of the 6-byte prefix table
+    const uint64_t t = i ? (uint64_t)(63 - __clzll((long long)i)) & 127u : 0;
+    const uint64_t u = hrand(s.seed, t, (uint64_t)pos, 4) >> 32;
+    return (uint8_t)(0x20 + ((u * 95u) >> 32));
+  }
+  if (s.kind == 0 || s.kind == 2) {
     uint64_t u = hrand(s.seed, i, (uint64_t)pos, 0) >> 32;
     return (uint8_t)(0x20 + ((u * 95u) >> 32));
   }
