@@ -40,6 +40,7 @@ def lib():
         L = ctypes.CDLL(_LIB)
         sig = {
             "eo_encode9": (U64, [P]),
+            "eo_set_key_bytes": (I32, [I32]),
             "eo_encode9_records": (None, [P, U64, P]),
             "eo_splitmix64_at": (U64, [U64, U64]),
             "eo_default_sample_size": (U64, [U64]),
@@ -58,7 +59,8 @@ def lib():
             "eo_mlp_forward32": (None, [P, P, U64, P]),
             "eo_mlp_forward64": (None, [P, P, U64, P]),
             "eo_mlp_grad64": (None, [P, P, P, U64, P]),
-            "eo_mlp_train64": (None, [P, P, P, U64, U32, U32, ctypes.c_double, P]),
+            "eo_mlp_train64": (None, [P, P, P, U64, U32, U32, ctypes.c_double, ctypes.c_double, P]),
+            "eo_mlp_lr_at": (ctypes.c_double, [U64, U64, ctypes.c_double, ctypes.c_double]),
             "eo_mlp_adam64": (None, [P, P, P, P, U64, ctypes.c_double]),
             "eo_radix_bins": (None, [P, U64, U32, P]),
             "eo_radix_splitters": (None, [U32, P]),
@@ -79,6 +81,22 @@ def lib():
 
 def _ptr(a):
     return None if a is None else a.ctypes.data
+
+
+class key_bytes:
+    """Context: the oracle's key is the first l bytes of each record (Sec. 4's
+    variable-length keys, 0-padded); 10 (the whole key field) outside it."""
+
+    def __init__(self, l: int):
+        self.l = l
+
+    def __enter__(self):
+        if lib().eo_set_key_bytes(self.l) != self.l:
+            raise ValueError("key length must be in [1, 10]")
+        return self
+
+    def __exit__(self, *a):
+        lib().eo_set_key_bytes(10)
 
 
 def encode9(key: bytes) -> int:
@@ -206,9 +224,11 @@ def validate(inp: np.ndarray, out: np.ndarray) -> int:
 
 # ---------------------------------------------------------------- monotone MLP CDF (mlp_oracle.cpp)
 MLP_FEATURES, MLP_HIDDEN = 12, 32
-MLP_PARAMS = 12 * 32 + 32 + 32 * 32 + 32 + 32 + 1  # 1505
+MLP_PARAMS = 12 * 32 + 32 + 32 * 32 + 32 + 32 + 1 + 12  # 1517
 MLP_SLICES = {"W1": (0, 384), "b1": (384, 416), "W2": (416, 1440), "b2": (1440, 1472), "w3": (1472, 1504),
-              "b3": (1504, 1505)}
+              "b3": (1504, 1505), "v": (1505, 1517)}
+MLP_WEIGHTS = ("W1", "W2", "w3", "v")  # projected onto >= 0
+MLP_BIASES = ("b1", "b2", "b3")
 
 
 def mlp_knots(sorted_sample: np.ndarray) -> np.ndarray:
@@ -256,14 +276,18 @@ def mlp_grad64(w: np.ndarray, phi: np.ndarray, y: np.ndarray) -> np.ndarray:
     return g
 
 
-def mlp_train64(w0: np.ndarray, phi: np.ndarray, y: np.ndarray, batch: int = 65536, epochs: int = 20,
-                lr: float = 1e-3):
+def mlp_train64(w0: np.ndarray, phi: np.ndarray, y: np.ndarray, batch: int = 8192, steps: int = 400,
+                lr: float = 1e-3, lr_min: float = 1e-5):
     w = np.array(w0, dtype=np.float64)
     phi = np.ascontiguousarray(phi, dtype=np.float64)
     y = np.ascontiguousarray(y, dtype=np.float64)
     loss = ctypes.c_double(0)
-    lib().eo_mlp_train64(_ptr(w), _ptr(phi), _ptr(y), y.size, batch, epochs, lr, ctypes.byref(loss))
+    lib().eo_mlp_train64(_ptr(w), _ptr(phi), _ptr(y), y.size, batch, steps, lr, lr_min, ctypes.byref(loss))
     return w, loss.value
+
+
+def mlp_lr_at(t: int, steps: int, lr: float = 1e-3, lr_min: float = 1e-5) -> float:
+    return float(lib().eo_mlp_lr_at(t, steps, lr, lr_min))
 
 
 def mlp_splitters(w: np.ndarray, T: np.ndarray, log2B: int) -> np.ndarray:

@@ -65,6 +65,26 @@ uint64_t encode9(const uint8_t* key) {
   return e;
 }
 
+// Variable-length keys (Sec. 4): keys of up to l characters, l the longest,
+// with ASCII = 0 at every position past a key's end.  Here the key is the
+// first g_key_bytes (l <= 10) bytes of each record; the bytes after them (and,
+// in a NUL-padded key field, the NULs past a shorter key's end) count as 0.
+// Reading of the padding rule: a 0 byte is below every printable character,
+// so by the saturation rule above it and every later digit encode as 0 -- a
+// shorter key sorts before every longer key it is a prefix of, as strncmp
+// orders NUL-terminated strings -- and byte order compares the padded keys.
+int g_key_bytes = 10;
+
+inline void key_of(const uint8_t* rec, uint8_t* k) {
+  for (int i = 0; i < kKey; ++i) k[i] = i < g_key_bytes ? rec[i] : 0;
+}
+
+inline uint64_t encode_rec(const uint8_t* rec) {
+  uint8_t k[kKey];
+  key_of(rec, k);
+  return encode9(k);
+}
+
 // The k-th output of the SplitMix64 generator seeded with `seed`
 // (state advances by the golden gamma; Steele, Lea, Flood 2014).
 uint64_t splitmix64_at(uint64_t seed, uint64_t k) {
@@ -288,7 +308,10 @@ inline uint32_t pid_of(const std::vector<uint32_t>& c, uint32_t P, uint32_t q) {
 }
 
 bool key_less(const uint8_t* recs, uint64_t a, uint64_t b) {
-  return std::memcmp(recs + a * kRecord, recs + b * kRecord, kKey) < 0;
+  uint8_t ka[kKey], kb[kKey];
+  key_of(recs + a * kRecord, ka);
+  key_of(recs + b * kRecord, kb);
+  return std::memcmp(ka, kb, kKey) < 0;
 }
 
 void stable_sort_indices(const uint8_t* recs, std::vector<uint64_t>& idx) {
@@ -354,8 +377,17 @@ extern "C" {
 
 uint64_t eo_encode9(const uint8_t* key) { return encode9(key); }
 
+// Key length l (1..10) of every later call: the key is a record's first l
+// bytes, padded with 0 bytes (Sec. 4's variable-length keys).  Returns l, or
+// 0 if l is out of range (the setting is then unchanged).
+int eo_set_key_bytes(int l) {
+  if (l < 1 || l > kKey) return 0;
+  g_key_bytes = l;
+  return l;
+}
+
 void eo_encode9_records(const uint8_t* recs, uint64_t n, uint64_t* out) {
-  for (uint64_t i = 0; i < n; ++i) out[i] = encode9(recs + i * kRecord);
+  for (uint64_t i = 0; i < n; ++i) out[i] = encode_rec(recs + i * kRecord);
 }
 
 uint64_t eo_splitmix64_at(uint64_t seed, uint64_t k) { return splitmix64_at(seed, k); }
@@ -374,7 +406,7 @@ uint64_t eo_default_sample_size(uint64_t n) {
 void eo_sample(const uint8_t* recs, uint64_t n, uint64_t S, uint64_t seed, uint64_t* out_enc) {
   for (uint64_t k = 0; k < S; ++k) {
     uint64_t i = (uint64_t)(((u128)splitmix64_at(seed, k) * (u128)n) >> 64);
-    out_enc[k] = encode9(recs + i * kRecord);
+    out_enc[k] = encode_rec(recs + i * kRecord);
   }
 }
 
@@ -441,7 +473,7 @@ int eo_sort(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint32_t 
   std::vector<uint32_t> q(n);
   std::vector<uint64_t> counts(B, 0);
   for (uint64_t i = 0; i < n; ++i) {
-    q[i] = fine_bin(rmi_cdf(m, encode9(in + i * kRecord)), log2B);
+    q[i] = fine_bin(rmi_cdf(m, encode_rec(in + i * kRecord)), log2B);
     counts[q[i]]++;
   }
   partition_sort_concat(in, n, q, counts, P, log2B, balance, out, q_out, pid_out, part_off, bin_counts, cuts_out);
@@ -460,7 +492,7 @@ int eo_classify(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, uint3
   Rmi m = rmi_fit(sample.data(), S, T, Dmax);
   uint32_t B = 1u << log2B;
   std::vector<uint64_t> counts(B, 0);
-  for (uint64_t i = 0; i < n; ++i) counts[fine_bin(rmi_cdf(m, encode9(in + i * kRecord)), log2B)]++;
+  for (uint64_t i = 0; i < n; ++i) counts[fine_bin(rmi_cdf(m, encode_rec(in + i * kRecord)), log2B)]++;
   std::vector<uint32_t> c = cuts_of(counts, P, log2B, n, balance);
   std::vector<uint64_t> C(B + 1, 0);
   for (uint32_t t = 0; t < B; ++t) C[t + 1] = C[t] + counts[t];
@@ -496,7 +528,10 @@ int eo_validate(const uint8_t* in, const uint8_t* out, uint64_t n) {
       seen[idx] = 1;
     }
     if (k > 0) {
-      int c = std::memcmp(out + (k - 1) * kRecord, r, kKey);
+      uint8_t ka[kKey], kb[kKey];
+      key_of(out + (k - 1) * kRecord, ka);
+      key_of(r, kb);
+      int c = std::memcmp(ka, kb, kKey);
       if (c > 0) bad |= 1;
       if (c == 0 && ok && idx < prev_idx) bad |= 4;
     }
@@ -538,7 +573,7 @@ int eo_sort_by_splitters(const uint8_t* in, uint64_t n, const uint64_t* t, uint3
   std::vector<uint32_t> q(n);
   std::vector<uint64_t> counts(B, 0);
   for (uint64_t i = 0; i < n; ++i) {
-    q[i] = bin_by_splitters(t, B, encode9(in + i * kRecord));
+    q[i] = bin_by_splitters(t, B, encode_rec(in + i * kRecord));
     counts[q[i]]++;
   }
   partition_sort_concat(in, n, q, counts, P, log2B, balance, out, q_out, pid_out, part_off, bin_counts, cuts_out);
@@ -651,7 +686,7 @@ int eo_sort_threads(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, u
         uint64_t a, b;
         ranges(k, &a, &b);
         for (uint64_t i = a; i < b; ++i) {
-          q[i] = fine_bin(rmi_cdf(m, encode9(in + i * kRecord)), log2B);
+          q[i] = fine_bin(rmi_cdf(m, encode_rec(in + i * kRecord)), log2B);
           cnt[k][q[i]]++;
         }
       });

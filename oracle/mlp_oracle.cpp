@@ -11,14 +11,20 @@
 //   feature phi_m(x) = W_m == 0 ? (x > T_m) : fp32(fp64(min(max(x - T_m, 0), W_m)) * R_m),
 //           W_m = T_{m+1} - T_m, R_m = 1.0 / fp64(W_m)     (m = 0..11; exact integer ramps)
 //   layer   h1_j = sigma(b1_j + sum_m W1_jm phi_m), h2_j = sigma(b2_j + sum_i W2_ji h1_i),
-//           z = b3 + sum_j w3_j h2_j, F = clamp(z, 0, 1); all weights >= 0
+//           z = b3 + sum_j w3_j h2_j + sum_m v_m phi_m, F = clamp(z, 0, 1); all weights
+//           (W1, W2, w3 and the linear skip v from the features to the output) >= 0
 //   sigma(z) = 0.5 + 0.5 z / (1 + |z|)
 //   sums    in index order as a chain of fused multiply-adds starting from the bias
+//           (the output: b3, then the w3 terms, then the v terms)
+//   start   v_m = 1/12, w3 = 0, b3 = 0: F starts as sum(phi) / 12, the linear
+//           interpolation of the sample CDF between the knots; the hidden layers
+//           start as structured soft steps (eo_mlp_init)
 //   bins    fine-bin splitters t_q = smallest x in [0, 95^9] with min(B-1, floor(B F(x))) >= q,
 //           found by bisection, then t_q = max(t_q, t_{q-1}); the fine bin of x is
 //           #{q >= 1 : t_q <= x}, monotone in x whatever FP32 rounding does to F
 //   training (FP64 here): MSE of F against rank/S on the sample, Adam
-//           (lr 1e-3, beta 0.9 / 0.999, eps 1e-8), weights projected to >= 0
+//           (beta 0.9 / 0.999, eps 1e-8) with the learning rate decayed from lr
+//           to lr_min over the steps by a half cosine, weights projected to >= 0
 //           after every step.
 // Parity: FP64 forward/backward pinned by closed forms and central finite
 // differences, the Adam step by its closed forms (first step, constant and
@@ -39,7 +45,7 @@ constexpr int kF = 12, kH = 32;
 constexpr uint64_t kEncTop = 630249409724609375ull;  // 95^9
 // parameter vector layout
 constexpr int oW1 = 0, oB1 = oW1 + kH * kF, oW2 = oB1 + kH, oB2 = oW2 + kH * kH, oW3 = oB2 + kH, oB3 = oW3 + kH,
-              kParams = oB3 + 1;  // 1505
+              oV = oB3 + 1, kParams = oV + kF;  // 1517
 
 struct Knots {
   uint64_t T[kF + 1];
@@ -90,6 +96,7 @@ float forward32(const float* w, const float* phi) {
   }
   float z = w[oB3];
   for (int j = 0; j < kH; ++j) z = std::fmaf(w[oW3 + j], h2[j], z);
+  for (int m = 0; m < kF; ++m) z = std::fmaf(w[oV + m], phi[m], z);
   return z < 0.0f ? 0.0f : (z > 1.0f ? 1.0f : z);
 }
 
@@ -119,6 +126,7 @@ void forward64(const double* w, const double* phi, Acts& a) {
   }
   double z = w[oB3];
   for (int j = 0; j < kH; ++j) z += w[oW3 + j] * a.h2[j];
+  for (int m = 0; m < kF; ++m) z += w[oV + m] * phi[m];
   a.z = z;
   a.F = z < 0.0 ? 0.0 : (z > 1.0 ? 1.0 : z);
 }
@@ -128,6 +136,7 @@ void backward64(const double* w, const double* phi, double y, const Acts& a, dou
   double dF = 2.0 * (a.F - y);
   double dz = (a.z > 0.0 && a.z < 1.0) ? dF : 0.0;
   g[oB3] += dz;
+  for (int m = 0; m < kF; ++m) g[oV + m] += dz * phi[m];
   double dp2[kH];
   for (int j = 0; j < kH; ++j) {
     g[oW3 + j] += dz * a.h2[j];
@@ -148,7 +157,7 @@ void backward64(const double* w, const double* phi, double y, const Acts& a, dou
   }
 }
 
-bool is_weight(int i) { return i < oB1 || (i >= oW2 && i < oB2) || (i >= oW3 && i < oB3); }
+bool is_weight(int i) { return i < oB1 || (i >= oW2 && i < oB2) || (i >= oW3 && i < oB3) || i >= oV; }
 
 }  // namespace
 
@@ -156,10 +165,11 @@ extern "C" {
 
 int eo_mlp_params(void) { return kParams; }
 
-// Structured starting point: hidden unit j of layer 1 is a soft step of
-// sum(phi) at 12 (j + 1/2) / 32, layer 2 passes it on, the output averages
-// (about the quantile interpolation the knots give), plus a 1 % jitter from
-// the SplitMix64 counter stream with seed 7.
+// Starting point: the output is the linear skip alone, F = sum(phi) / 12 (the
+// interpolation of the sample CDF between the knots); the hidden layers start
+// structured -- hidden unit j of layer 1 a soft step of sum(phi) at
+// 12 (j + 1/2) / 32, layer 2 passing it on -- with a 1 % jitter from the
+// SplitMix64 counter stream with seed 7, ready for w3 to take them in.
 void eo_mlp_init(float* w) {
   auto jitter = [](uint32_t i) {
     uint64_t z = 7ull + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
@@ -168,7 +178,7 @@ void eo_mlp_init(float* w) {
     z ^= z >> 31;
     return (float)(z >> 40) * (1.0f / 16777216.0f);
   };
-  const float k = 8.0f, a = 4.0f, amp = (a / 2) / (1 + a / 2);
+  const float k = 8.0f, a = 4.0f;
   for (int i = 0; i < kParams; ++i) {
     float v;
     if (i < oB1) v = k * (1.0f + 0.01f * jitter(i));
@@ -177,8 +187,8 @@ void eo_mlp_init(float* w) {
       int j = (i - oW2) / kH, c = (i - oW2) % kH;
       v = j == c ? a * (1.0f + 0.01f * jitter(i)) : 0.01f * jitter(i);
     } else if (i < oW3) v = -a / 2;
-    else if (i < oB3) v = 1.0f / (32.0f * amp);
-    else v = -(0.5f - 0.5f * amp) / amp;
+    else if (i < oV) v = 0.0f;  // w3 and b3
+    else v = 1.0f / 12.0f;
     w[i] = v;
   }
 }
@@ -242,25 +252,31 @@ void eo_mlp_adam64(double* w, const double* g, double* m, double* v, uint64_t t,
   }
 }
 
-// FP64 training (Adam + projection) on features/labels; minibatch b holds
+// The learning rate of step t (1-based) of `steps`: a half cosine from lr to lr_min.
+double eo_mlp_lr_at(uint64_t t, uint64_t steps, double lr, double lr_min) {
+  const double pi = 3.14159265358979323846;
+  const double f = steps > 1 ? (double)(t - 1) / (double)(steps - 1) : 0.0;
+  return lr_min + (lr - lr_min) * 0.5 * (1.0 + std::cos(pi * f));
+}
+
+// FP64 training (Adam + projection) on features/labels: `steps` minibatch
+// steps, step t taking minibatch (t - 1) mod nb, where minibatch b holds
 // samples b, b + nb, b + 2 nb, ... (nb = ceil(n / batch)); w in/out.
-void eo_mlp_train64(double* w, const double* phi, const double* y, uint64_t n, uint32_t batch, uint32_t epochs,
-                    double lr, double* loss_out) {
+void eo_mlp_train64(double* w, const double* phi, const double* y, uint64_t n, uint32_t batch, uint32_t steps,
+                    double lr, double lr_min, double* loss_out) {
   std::vector<double> mom(kParams, 0.0), vel(kParams, 0.0), g(kParams);
   uint64_t nb = (n + batch - 1) / batch;
-  uint64_t t = 0;
   Acts a;
-  for (uint32_t ep = 0; ep < epochs; ++ep) {
-    for (uint64_t b = 0; b < nb; ++b) {
-      for (int i = 0; i < kParams; ++i) g[i] = 0.0;
-      uint64_t cnt = 0;
-      for (uint64_t s = b; s < n; s += nb, ++cnt) {
-        forward64(w, phi + s * kF, a);
-        backward64(w, phi + s * kF, y[s], a, g.data());
-      }
-      for (int i = 0; i < kParams; ++i) g[i] /= (double)cnt;
-      eo_mlp_adam64(w, g.data(), mom.data(), vel.data(), ++t, lr);
+  for (uint64_t t = 1; t <= steps; ++t) {
+    const uint64_t b = (t - 1) % nb;
+    for (int i = 0; i < kParams; ++i) g[i] = 0.0;
+    uint64_t cnt = 0;
+    for (uint64_t s = b; s < n; s += nb, ++cnt) {
+      forward64(w, phi + s * kF, a);
+      backward64(w, phi + s * kF, y[s], a, g.data());
     }
+    for (int i = 0; i < kParams; ++i) g[i] /= (double)cnt;
+    eo_mlp_adam64(w, g.data(), mom.data(), vel.data(), t, eo_mlp_lr_at(t, steps, lr, lr_min));
   }
   if (loss_out) {
     double l = 0.0;

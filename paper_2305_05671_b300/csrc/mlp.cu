@@ -7,8 +7,14 @@
 //   feature phi_m = W_m == 0 ? (x > T_m) : fp32(fp64(clamp(x - T_m, 0, W_m)) * R_m),
 //           W_m = T_{m+1} - T_m, R_m = 1 / fp64(W_m)
 //   layers  fused multiply-add chains in index order from the bias,
-//           sigma(z) = 0.5 + 0.5 z / (1 + |z|), F = clamp(z, 0, 1)
+//           sigma(z) = 0.5 + 0.5 z / (1 + |z|); the output adds a non-negative
+//           linear skip of the features: z = b3 + sum w3_j h2_j + sum v_m phi_m,
+//           F = clamp(z, 0, 1)
+//   start   F = sum(phi) / 12 (v = 1/12, w3 = b3 = 0): the interpolation of the
+//           sample CDF between the knots, which training then refines
 //   splitters by bisection on floor(B F), made non-decreasing by a running max
+#include <cmath>
+
 #include "common.cuh"
 #include "mlp.cuh"
 
@@ -16,7 +22,7 @@ namespace elsar {
 
 constexpr int kMF = 12, kMH = 32;
 constexpr int oW1 = 0, oB1 = oW1 + kMH * kMF, oW2 = oB1 + kMH, oB2 = oW2 + kMH * kMH, oW3 = oB2 + kMH, oB3 = oW3 + kMH,
-              kMlpParams = oB3 + 1;  // 1505
+              oV = oB3 + 1, kMlpParams = oV + kMF;  // 1517
 static_assert(kMlpParams == kMlpParamCount, "parameter layout");
 
 struct MlpKnots {
@@ -70,6 +76,8 @@ __device__ __forceinline__ float mlp_forward(const float* __restrict__ w, const 
     for (int i = 0; i < kMH; ++i) acc = __fmaf_rn(w[oW2 + j * kMH + i], h1[i], acc);
     z = __fmaf_rn(w[oW3 + j], sigma32(acc), z);
   }
+#pragma unroll
+  for (int m = 0; m < kMF; ++m) z = __fmaf_rn(w[oV + m], phi[m], z);
   return z < 0.0f ? 0.0f : (z > 1.0f ? 1.0f : z);
 }
 
@@ -202,10 +210,10 @@ __global__ void features_kernel(const uint64_t* __restrict__ x, uint64_t n, cons
   }
 }
 
-// Structured start: hidden unit j of layer 1 is a soft step of sum(phi) at
-// 12 (j + 1/2) / 32, layer 2 passes it on, the output averages -- about the
-// quantile interpolation the knots already give -- plus a 1 % jitter from a
-// counter-based generator (seed 7).
+// Start: the output is the linear skip alone, F = sum(phi) / 12; the hidden
+// layers start structured -- hidden unit j of layer 1 a soft step of sum(phi)
+// at 12 (j + 1/2) / 32, layer 2 passing it on -- with a 1 % jitter from a
+// counter-based generator (seed 7), ready for w3 to take them in.
 __device__ __forceinline__ float jitter(uint32_t i) {
   uint64_t z = 7ull + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ull;
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -215,7 +223,7 @@ __device__ __forceinline__ float jitter(uint32_t i) {
 }
 
 __global__ void init_kernel(float* w, float* m, float* v) {
-  const float k = 8.0f, a = 4.0f, amp = (a / 2) / (1 + a / 2);
+  const float k = 8.0f, a = 4.0f;
   for (int i = threadIdx.x; i < kMlpParams; i += blockDim.x) {
     float val;
     if (i < oB1) val = k * (1.0f + 0.01f * jitter(i));
@@ -224,8 +232,8 @@ __global__ void init_kernel(float* w, float* m, float* v) {
       const int j = (i - oW2) / kMH, c = (i - oW2) % kMH;
       val = (j == c ? a * (1.0f + 0.01f * jitter(i)) : 0.01f * jitter(i));
     } else if (i < oW3) val = -a / 2;
-    else if (i < oB3) val = 1.0f / (32.0f * amp);
-    else val = -(0.5f - 0.5f * amp) / amp;
+    else if (i < oV) val = 0.0f;  // w3 and b3
+    else val = 1.0f / 12.0f;
     w[i] = val;
     m[i] = 0.0f;
     v[i] = 0.0f;
@@ -280,6 +288,8 @@ __global__ void __launch_bounds__(kChunk) grad_kernel(const float* __restrict__ 
       d2[me][j] = dsigma32(t);
       z = __fmaf_rn(w[oW3 + j], hj, z);
     }
+#pragma unroll
+    for (int m = 0; m < kMF; ++m) z = __fmaf_rn(w[oV + m], phi[me][m], z);
     const float F = z < 0.0f ? 0.0f : (z > 1.0f ? 1.0f : z);
     const float g = (live && z > 0.0f && z < 1.0f) ? 2.0f * (F - y) * inv_cnt : 0.0f;
     dz[me] = g;
@@ -315,8 +325,11 @@ __global__ void __launch_bounds__(kChunk) grad_kernel(const float* __restrict__ 
       } else if (p < oB3) {
         const int j = p - oW3;
         for (int s2 = 0; s2 < kChunk; ++s2) sum = __fmaf_rn(dz[s2], h2[s2][j], sum);
-      } else {
+      } else if (p == oB3) {
         for (int s2 = 0; s2 < kChunk; ++s2) sum += dz[s2];
+      } else {
+        const int m = p - oV;
+        for (int s2 = 0; s2 < kChunk; ++s2) sum = __fmaf_rn(dz[s2], phi[s2][m], sum);
       }
       acc[r] += sum;
     }
@@ -338,7 +351,7 @@ __global__ void reduce_partials_kernel(const float* __restrict__ partial, int np
 }
 
 __device__ __forceinline__ bool is_weight(int i) {
-  return i < oB1 || (i >= oW2 && i < oB2) || (i >= oW3 && i < oB3);
+  return i < oB1 || (i >= oW2 && i < oB2) || (i >= oW3 && i < oB3) || i >= oV;
 }
 
 // Adam on the summed partial gradients (fixed order), weights projected to >= 0.
@@ -386,19 +399,36 @@ cudaError_t mlp_train(const MlpTrainArgs& a) {
   init_kernel<<<1, 256, 0, st>>>(a.w, a.m, a.v);
   *a.launches += 3;
   const uint64_t per = a.ntrain / nb, extra = a.ntrain % nb;
+  // one CTA per chunk of 64 samples of the largest minibatch, at most a.grid
+  const int grid = (int)umin64((uint64_t)a.grid, (per + 1 + kChunk - 1) / kChunk);
+  const double pi = 3.14159265358979323846;
   double p1 = 1.0, p2 = 1.0;
-  for (uint32_t ep = 0; ep < a.epochs; ++ep) {
-    for (uint64_t b = 0; b < nb; ++b) {
-      const uint64_t b0 = b * per + (b < extra ? b : extra);
-      const uint32_t cnt = (uint32_t)(per + (b < extra ? 1 : 0));
-      grad_kernel<<<a.grid, kChunk, 0, st>>>(a.w, a.phi, a.y, b0, cnt, 1.0f / (float)cnt, a.partial);
-      p1 *= 0.9;
-      p2 *= 0.999;
-      adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(a.partial, a.grid, a.w, a.m, a.v, a.lr,
-                                                             (float)(1.0 / (1.0 - p1)), (float)(1.0 / (1.0 - p2)));
-      *a.launches += 2;
-    }
+  for (uint32_t t = 1; t <= a.steps; ++t) {
+    const uint64_t b = (t - 1) % nb;  // minibatch b holds training samples b, b + nb, ...
+    const uint64_t b0 = b * per + (b < extra ? b : extra);
+    const uint32_t cnt = (uint32_t)(per + (b < extra ? 1 : 0));
+    grad_kernel<<<grid, kChunk, 0, st>>>(a.w, a.phi, a.y, b0, cnt, 1.0f / (float)cnt, a.partial);
+    p1 *= 0.9;
+    p2 *= 0.999;
+    // half-cosine decay of the learning rate from lr to lr_min over the steps
+    const double f = a.steps > 1 ? (double)(t - 1) / (double)(a.steps - 1) : 0.0;
+    const double lr = a.lr_min + (a.lr - a.lr_min) * 0.5 * (1.0 + cos(pi * f));
+    adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(a.partial, grid, a.w, a.m, a.v, (float)lr,
+                                                           (float)(1.0 / (1.0 - p1)), (float)(1.0 / (1.0 - p2)));
+    *a.launches += 2;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_adam_step(float* w, const float* grad, float* m, float* v, uint32_t t, float lr, cudaStream_t st) {
+  // the trainer's bias corrections: running products of the decay rates in FP64, then one rounding
+  double p1 = 1.0, p2 = 1.0;
+  for (uint32_t k = 0; k < t; ++k) {
+    p1 *= 0.9;
+    p2 *= 0.999;
+  }
+  adam_kernel<<<(kMlpParams + 255) / 256, 256, 0, st>>>(grad, 1, w, m, v, lr, (float)(1.0 / (1.0 - p1)),
+                                                         (float)(1.0 / (1.0 - p2)));
   return cudaGetLastError();
 }
 

@@ -57,7 +57,7 @@ def test_gradient_matches_fp64_chain_rule(spec):
     T = oracle.mlp_knots(x)
     y = (np.arange(x.size) / x.size).astype(np.float32)
     w = _weights(4)
-    d_g = torch.empty(1505, dtype=torch.float32, device="cuda")
+    d_g = torch.empty(oracle.MLP_PARAMS, dtype=torch.float32, device="cuda")
     elsar.mlp_grad(torch.from_numpy(w).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(x).cuda(),
                    torch.from_numpy(y).cuda(), x.size, d_g)
     got = d_g.cpu().numpy().astype(np.float64)
@@ -98,7 +98,9 @@ def test_trained_network_improves_and_is_judged(spec):
     p = elsar.Params(num_partitions=256, sample_size=S, seed=9, model_kind=elsar.MODEL_MLP)
     hdr, _, _ = _fit(host, n, p)
     w, T = hdr["mlp_w"], hdr["mlp_knots"]
-    assert np.all(w[0:384] >= 0) and np.all(w[416:1440] >= 0) and np.all(w[1472:1504] >= 0)
+    for k in oracle.MLP_WEIGHTS:
+        a, b = oracle.MLP_SLICES[k]
+        assert np.all(w[a:b] >= 0), k
     x = np.sort(oracle.sample(host, S, 9))
     assert np.array_equal(T, oracle.mlp_knots(x))  # knots from the same sorted sample
     y = np.arange(S) / S
@@ -131,28 +133,35 @@ def test_sort_output_exact_with_network(spec):
     assert st["model_used"] in (0, 1) and (st["model_used"] == 1) == (st["fallback_reason"] == 0)
 
 
-def test_network_vs_rmi_gain_report():
-    """What the trained network gains over the RMI alone, on skewed keys: both
-    models' partition imbalance under the paper's rule and the sort time.  The
-    judge must keep the network only if it is at least as balanced."""
+def test_network_gain_over_the_rmi():
+    """What the trained network gains over the method without it.  Under the
+    paper's cut rule (partition = floor(P F)) the partitions are as even as the
+    model is accurate.  On uniform keys the RMI, fitted to every wiggle of its
+    1 % sample, leaves partitions up to a third above the mean at 1024
+    partitions; the network, a smooth function of 12 features, stays close to
+    the mean, so the held-out judge keeps it and the full-data check passes.
+    On product-Zipf keys the network cannot follow the fractal CDF, and the
+    judge falls back to the RMI (reason 2)."""
     n, P = 5_000_000, 1024
-    spec = recgen.KeySpec("zipf", s=1.3, dup=0.10, seed=5)
-    d_in = torch.empty(n * 100, dtype=torch.uint8, device="cuda")
-    recgen.generate_gpu(d_in, n, spec)
-    d_out = torch.empty_like(d_in)
     res = {}
-    for kind in (elsar.MODEL_RMI, elsar.MODEL_MLP):
-        p = elsar.Params(num_partitions=P, model_kind=kind, balance=elsar.BALANCE_PAPER, sample_size=2_000_000)
-        ws = elsar.alloc_workspace(n, p)
-        elsar.sort(d_in, d_out, n, p, ws=ws, stats=True)
-        st = elsar.sort(d_in, d_out, n, p, ws=ws, stats=True)
-        res[kind] = st
-    rmi, mlp = res[elsar.MODEL_RMI], res[elsar.MODEL_MLP]
-    print("\nRMI:", {k: rmi[k] for k in ("max_partition", "max_bin", "oversize_items", "pass_ms")})
-    print("MLP requested:", {k: mlp[k] for k in ("max_partition", "max_bin", "oversize_items", "pass_ms",
-                                                 "model_used", "fallback_reason")})
-    if mlp["model_used"] == elsar.MODEL_MLP:
-        assert mlp["max_partition"] <= 1.1 * n / P  # the full-data check would have reverted otherwise
-    else:
-        assert mlp["fallback_reason"] in (1, 2, 3)
-        assert mlp["max_partition"] == rmi["max_partition"]
+    for name, spec in (("uniform", recgen.KeySpec("uniform", seed=2)),
+                       ("zipf13", recgen.KeySpec("zipf", s=1.3, dup=0.10, seed=5))):
+        d_in = torch.empty(n * 100, dtype=torch.uint8, device="cuda")
+        recgen.generate_gpu(d_in, n, spec)
+        d_out = torch.empty_like(d_in)
+        for kind in (elsar.MODEL_RMI, elsar.MODEL_MLP):
+            p = elsar.Params(num_partitions=P, model_kind=kind, balance=elsar.BALANCE_PAPER, sample_size=200_000)
+            st = elsar.sort(d_in, d_out, n, p, stats=True)
+            res[name, kind] = st
+        torch.cuda.synchronize()
+        del d_in, d_out
+    for (name, kind), st in res.items():
+        print(f"\n{name} {'network' if kind else 'rmi'}: imbalance {st['max_partition'] * P / n:.4f} "
+              f"model_used {st['model_used']} fallback {st['fallback_reason']} judge "
+              f"{st['judge_rmi_max']}/{st['judge_mlp_max']} of {st['judge_buckets']} fit {st['pass_ms'][0]:.2f} ms")
+    u_rmi, u_net = res["uniform", elsar.MODEL_RMI], res["uniform", elsar.MODEL_MLP]
+    assert u_net["model_used"] == elsar.MODEL_MLP and u_net["fallback_reason"] == 0
+    assert u_net["max_partition"] * P / n <= 1.1 < u_rmi["max_partition"] * P / n
+    z_net = res["zipf13", elsar.MODEL_MLP]
+    assert z_net["model_used"] == elsar.MODEL_RMI and z_net["fallback_reason"] == 2
+    assert z_net["max_partition"] == res["zipf13", elsar.MODEL_RMI]["max_partition"]

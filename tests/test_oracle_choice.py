@@ -23,7 +23,7 @@ def _log2B(orc, n):
 
 
 def _const_net(c):
-    w = np.zeros(1505, dtype=np.float32)
+    w = np.zeros(1517, dtype=np.float32)
     w[1504] = c  # b3: with w3 = 0 the network outputs c everywhere
     return w
 
@@ -32,7 +32,7 @@ def _one_path(b3):
     """h1_0 = sigma(-6 + sum(phi)), h2_0 = sigma(h1_0), F = b3 + w3 * h2_0.
     At the first knot every ramp is 0: h1 = sigma(-6) = 1/14, h2 = sigma(1/14) = 8/15.
     At the last knot every ramp is 1: h1 = sigma(6) = 13/14, h2 = sigma(13/14) = 20/27."""
-    w = np.zeros(1505, dtype=np.float32)
+    w = np.zeros(1517, dtype=np.float32)
     w[0:12] = 1.0  # W1[0][m]
     w[384] = -6.0  # b1[0]
     w[416] = 1.0  # W2[0][0]

@@ -8,22 +8,28 @@ monotonicity, and a trained network beating a single least-squares line.
 import numpy as np
 import pytest
 
-S = oracle_slices = None
+NP = 1517  # W1[32][12], b1[32], W2[32][32], b2[32], w3[32], b3, v[12]
 
 
 def _w(rng, scale=1.0):
-    w = rng.random(1505) * scale
+    w = rng.random(NP) * scale
     w[384:416] = rng.normal(0, 1, 32)  # b1
     w[1440:1472] = rng.normal(0, 1, 32)  # b2
     w[1472:1504] *= 2.0 / 32  # w3
     w[1504] = 0.0
     w[0:384] *= 2.0 / 12
     w[416:1440] *= 2.0 / 32
+    w[1505:1517] *= 0.5 / 12  # v
     return w
 
 
+def test_layout(orc):
+    assert orc.MLP_PARAMS == NP == orc.lib().eo_mlp_params()
+    assert sum(b - a for a, b in orc.MLP_SLICES.values()) == NP
+
+
 def test_closed_form_forward(orc):
-    w = np.zeros(1505)
+    w = np.zeros(NP)
     w[1472:1504] = 0.02
     w[1504] = 0.3
     phi = np.random.default_rng(0).random((5, 12))
@@ -31,7 +37,7 @@ def test_closed_form_forward(orc):
     assert np.allclose(orc.mlp_forward64(w, phi), 0.3 + 0.32)
     assert np.allclose(orc.mlp_forward32(w.astype(np.float32), phi.astype(np.float32)), 0.62, atol=1e-7)
     # sigma(1) = 3/4 for one path: W1[0,0] = 1, phi_0 = 1 -> h1_0 = 3/4; W2[0,0] = 4 -> p2_0 = 3 -> h2_0 = 7/8
-    w = np.zeros(1505)
+    w = np.zeros(NP)
     w[0] = 1.0
     w[416] = 4.0
     w[1472] = 1.0
@@ -43,6 +49,24 @@ def test_closed_form_forward(orc):
     assert orc.mlp_forward64(w, phi)[0] == 1.0
     w[1504] = -5.0
     assert orc.mlp_forward64(w, phi)[0] == 0.0
+    # the linear skip alone: F = sum_m v_m phi_m
+    w = np.zeros(NP)
+    w[1505:1517] = np.arange(1, 13) / 78.0  # sums to 1
+    phi = np.random.default_rng(6).random((7, 12))
+    assert np.allclose(orc.mlp_forward64(w, phi), phi @ (np.arange(1, 13) / 78.0), rtol=1e-14)
+
+
+def test_start_is_the_knot_interpolation(orc):
+    """The starting network is F = sum(phi) / 12: at the knots T_m it is m / 12
+    (up to FP32 rounding), linear in between."""
+    x = np.sort(np.random.default_rng(9).integers(0, 95**9, 20001, dtype=np.uint64))
+    T = orc.mlp_knots(x)
+    w = orc.mlp_init()
+    F = orc.mlp_forward32(w, orc.mlp_features(T, T))
+    assert np.allclose(F, np.arange(13) / 12, atol=2e-7)
+    mid = T[:12] + (T[1:] - T[:12]) // np.uint64(2)
+    Fm = orc.mlp_forward32(w, orc.mlp_features(T, mid))
+    assert np.allclose(Fm, (np.arange(12) + 0.5) / 12, atol=1e-6)
 
 
 def test_features_are_ramps_between_knots(orc):
@@ -69,7 +93,7 @@ def test_backward_matches_central_differences(orc):
     F = orc.mlp_forward64(w, phi)
     assert np.all((F > 0) & (F < 1))  # away from the clamp's kinks
     g = orc.mlp_grad64(w, phi, y)
-    idx = np.concatenate([rng.choice(1505, 60, replace=False), [0, 383, 384, 416, 1439, 1440, 1472, 1504]])
+    idx = np.concatenate([rng.choice(NP, 60, replace=False), [0, 383, 384, 416, 1439, 1440, 1472, 1504, 1505, 1516]])
 
     def loss(v):
         return np.mean((orc.mlp_forward64(v, phi) - y) ** 2)
@@ -104,7 +128,7 @@ def test_nonnegative_weights_make_it_monotone(orc):
         assert np.all(np.diff(F) >= -1e-12)
 
 
-def test_training_beats_a_least_squares_line(orc, gen):
+def test_training_beats_its_start_and_a_least_squares_line(orc, gen):
     n = 200_000
     recs = gen.generate_cpu(n, gen.KeySpec("zipf", s=1.3, dup=0.1, seed=5))
     x = np.sort(orc.sample(recs, 20000, 1))
@@ -113,15 +137,25 @@ def test_training_beats_a_least_squares_line(orc, gen):
     phi = orc.mlp_features(T, x).astype(np.float64)
     w0 = orc.mlp_init().astype(np.float64)
     init_mse = np.mean((orc.mlp_forward64(w0, phi) - y) ** 2)
-    w, loss = orc.mlp_train64(w0, phi, y, batch=4096, epochs=20, lr=1e-3)
+    w, loss = orc.mlp_train64(w0, phi, y, batch=4096, steps=150, lr=1e-3, lr_min=1e-5)
     assert loss < init_mse
     slope, icpt = np.polyfit(x.astype(np.float64), y, 1)
     line_mse = np.mean((np.clip(slope * x.astype(np.float64) + icpt, 0, 1) - y) ** 2)
     assert loss < line_mse / 10
     # projection keeps every weight >= 0
-    for k in ("W1", "W2", "w3"):
+    for k in orc.MLP_WEIGHTS:
         a, b = orc.MLP_SLICES[k]
         assert np.all(w[a:b] >= 0)
+
+
+def test_learning_rate_schedule_closed_form(orc):
+    """Half-cosine decay: lr at the first step, lr_min at the last, their mean
+    half way, and the cosine's value in between."""
+    assert orc.mlp_lr_at(1, 101, 1e-3, 1e-5) == pytest.approx(1e-3, rel=1e-15)
+    assert orc.mlp_lr_at(101, 101, 1e-3, 1e-5) == pytest.approx(1e-5, rel=1e-12)
+    assert orc.mlp_lr_at(51, 101, 1e-3, 1e-5) == pytest.approx((1e-3 + 1e-5) / 2, rel=1e-12)
+    # a quarter of the way: cos(pi/4) = sqrt(2)/2
+    assert orc.mlp_lr_at(26, 101, 1e-3, 1e-5) == pytest.approx(1e-5 + 0.99e-3 * (1 + 2**-0.5) / 2, rel=1e-12)
 
 
 def test_splitters_reproduce_the_fp32_bins(orc):
@@ -140,13 +174,13 @@ def test_splitters_reproduce_the_fp32_bins(orc):
 
 
 # ---------------------------------------------------------------- Adam (Kingma & Ba 2015, Algorithm 1)
-W_SLICES = ("W1", "W2", "w3")
+W_SLICES = ("W1", "W2", "w3", "v")
 B_SLICES = ("b1", "b2", "b3")
 LR = 1e-3
 
 
 def _mask(orc, names):
-    m = np.zeros(1505, bool)
+    m = np.zeros(NP, bool)
     for k in names:
         a, b = orc.MLP_SLICES[k]
         m[a:b] = True
@@ -158,9 +192,9 @@ def test_adam_first_step_moves_each_parameter_by_lr(orc):
     vhat = g^2 exactly, so step 1 moves every parameter by lr * |g| / (|g| + eps)
     against its gradient -- whatever the sign or size of g."""
     rng = np.random.default_rng(10)
-    w0 = rng.random(1505) + 1.0  # far from the projection
-    g = rng.normal(0, 1, 1505) * 10.0 ** rng.integers(-4, 3, 1505)
-    w, m, v = orc.mlp_adam64(w0, g, np.zeros(1505), np.zeros(1505), 1, LR)
+    w0 = rng.random(NP) + 1.0  # far from the projection
+    g = rng.normal(0, 1, NP) * 10.0 ** rng.integers(-4, 3, NP)
+    w, m, v = orc.mlp_adam64(w0, g, np.zeros(NP), np.zeros(NP), 1, LR)
     assert np.allclose(w - w0, -LR * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=0)
     assert np.allclose(m, 0.1 * g, rtol=1e-15) and np.allclose(v, 0.001 * g * g, rtol=1e-15)
 
@@ -170,10 +204,10 @@ def test_adam_constant_gradient_keeps_step_lr(orc):
     (the corrections 1 - beta^t undo the zero start exactly), so every step is
     lr * g / (|g| + eps): a correction taken at the wrong t changes the step."""
     rng = np.random.default_rng(11)
-    g = rng.normal(0, 1, 1505)
-    w = rng.random(1505) + 1.0
-    m = np.zeros(1505)
-    v = np.zeros(1505)
+    g = rng.normal(0, 1, NP)
+    w = rng.random(NP) + 1.0
+    m = np.zeros(NP)
+    v = np.zeros(NP)
     for t in range(1, 6):
         w_prev = w
         w, m, v = orc.mlp_adam64(w, g, m, v, t, LR)
@@ -185,9 +219,9 @@ def test_adam_alternating_gradient_second_step(orc):
     so mhat_2 = -1/19; v_2 = 0.999 * 0.001 + 0.001 = 0.001999 = 1 - 0.999^2, so
     vhat_2 = 1.  The second step is therefore +lr / 19 / (1 + eps).  (With the
     two decay rates swapped it would be about +lr / 2000.)"""
-    w0 = np.full(1505, 1.0)
-    w1, m, v = orc.mlp_adam64(w0, np.ones(1505), np.zeros(1505), np.zeros(1505), 1, LR)
-    w2, m, v = orc.mlp_adam64(w1, -np.ones(1505), m, v, 2, LR)
+    w0 = np.full(NP, 1.0)
+    w1, m, v = orc.mlp_adam64(w0, np.ones(NP), np.zeros(NP), np.zeros(NP), 1, LR)
+    w2, m, v = orc.mlp_adam64(w1, -np.ones(NP), m, v, 2, LR)
     assert np.allclose(m, -0.01, rtol=1e-12) and np.allclose(v, 0.001999, rtol=1e-12)
     assert np.allclose(w2 - w1, LR / 19 / (1 + 1e-8), rtol=1e-10)
 
@@ -195,12 +229,12 @@ def test_adam_alternating_gradient_second_step(orc):
 def test_adam_projects_weights_not_biases(orc):
     """After the step the weights (W1, W2, w3) are projected onto >= 0, which
     keeps the network monotone; the biases are free to go negative."""
-    g = np.ones(1505)  # every parameter steps down by lr
-    w, _, _ = orc.mlp_adam64(np.zeros(1505), g, np.zeros(1505), np.zeros(1505), 1, LR)
+    g = np.ones(NP)  # every parameter steps down by lr
+    w, _, _ = orc.mlp_adam64(np.zeros(NP), g, np.zeros(NP), np.zeros(NP), 1, LR)
     wm, bm = _mask(orc, W_SLICES), _mask(orc, B_SLICES)
     assert np.all(w[wm] == 0.0)
     assert np.allclose(w[bm], -LR / (1 + 1e-8), rtol=1e-12)
-    assert wm.sum() + bm.sum() == 1505
+    assert wm.sum() + bm.sum() == NP
 
 
 def test_training_one_full_batch_is_gradient_then_adam(orc):
@@ -211,9 +245,9 @@ def test_training_one_full_batch_is_gradient_then_adam(orc):
     w0 = _w(rng)
     phi = rng.random((300, 12))
     y = rng.random(300)
-    w, _ = orc.mlp_train64(w0, phi, y, batch=300, epochs=1, lr=LR)
+    w, _ = orc.mlp_train64(w0, phi, y, batch=300, steps=1, lr=LR, lr_min=LR)
     g = orc.mlp_grad64(w0, phi, y)
-    want, _, _ = orc.mlp_adam64(w0, g, np.zeros(1505), np.zeros(1505), 1, LR)
+    want, _, _ = orc.mlp_adam64(w0, g, np.zeros(NP), np.zeros(NP), 1, LR)
     assert np.array_equal(w, want)
 
 
