@@ -16,8 +16,10 @@ python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -33,10 +35,10 @@ RECORD = 100
 # pair, read the 100-byte record, write it to its place in the output
 SORT_GATHER_BYTES = 16 + 100 + 100
 CPU_SAMPLE = 10_000_000  # records of each key set sorted by the oracle for the CPU baseline
-# DRAM bytes per record of sort_gather_kernel (dram__bytes_read.sum + dram__bytes_write.sum
-# of one ncu launch divided by its records), from the capture summarised in
-# profiles/sort_gather_kernel_uniform_20M.md; None once the kernel changes.
-SORT_GATHER_TRAFFIC_PER_RECORD = 356.5  # ncu dram bytes per record of sort_gather_kernel, 20M uniform and Zipf (profiles/)
+# The sort kernel's sources: a DRAM-traffic figure taken by ncu counts only
+# while these files are byte for byte the ones it was taken on.
+SORT_KERNEL_SOURCES = ("paper_2305_05671_b300/csrc/sort.cu", "paper_2305_05671_b300/csrc/common.cuh")
+TRAFFIC_PROFILE = "profiles/sort_gather_kernel_traffic.md"
 METRIC = "GB/s sorted (100-B recs), learned+batched vs plain on 1 B300; % HBM roofline"
 
 
@@ -65,6 +67,50 @@ def workload_config(extra=None):
     if extra:
         cfg.update(extra)
     return cfg
+
+
+def sort_kernel_digest() -> str:
+    h = hashlib.sha256()
+    for f in SORT_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """(DRAM bytes per record, digest) of the sort kernel from the committed ncu
+    summary, or (None, reason) when there is none or the kernel has changed
+    since it was captured."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_PROFILE)) as f:
+            txt = f.read()
+    except OSError:
+        return None, "no ncu traffic summary"
+    d = re.search(r"source digest:\s*`?([0-9a-f]{16})", txt)
+    v = re.search(r"dram bytes per record:\s*`?([0-9.]+)", txt)
+    if not d or not v:
+        return None, "traffic summary unreadable"
+    if d.group(1) != sort_kernel_digest():
+        return None, f"kernel changed since the ncu capture (digest {d.group(1)})"
+    return float(v.group(1)), d.group(1)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def measured_peaks():
@@ -126,23 +172,36 @@ class Clocks:
         return {"sm_mhz": statistics.median(load), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(args, world_rank=0):
-    """The oracle, as it stands, on a bounded sample of each key set (the first --cpu-sample records)."""
+def cpu_baseline(args, world_rank=0, single=True):
+    """The oracle, as it stands, on a bounded sample of each key set (the first
+    --cpu-sample records): the paper's CPU design over all host cores
+    (classification in ranges, partitions sorted in parallel), and, for
+    comparison, the single-threaded oracle on the same sample."""
     import oracle
     import recgen
 
     m = args.cpu_sample
-    tot_bytes, tot_s = 0, 0.0
+    cores = host_cores()
+    tot_bytes, t_all, t_one = 0, 0.0, 0.0
     for wl in workloads():
         host = recgen.generate_cpu(wl["n"], wl["spec"], i0=0, count=m)
         log2B = oracle.default_fine_log2(m, PARTITIONS)
+        S = oracle.default_sample_size(m)
         t0 = time.perf_counter()
-        oracle.sort(host, PARTITIONS, log2B, S=oracle.default_sample_size(m), seed=0x5EED, balance=1)
-        tot_s += time.perf_counter() - t0
+        oracle.sort_threads(host, PARTITIONS, log2B, S=S, seed=0x5EED, balance=1, threads=cores)
+        t_all += time.perf_counter() - t0
+        if single:
+            t0 = time.perf_counter()
+            oracle.sort(host, PARTITIONS, log2B, S=S, seed=0x5EED, balance=1)
+            t_one += time.perf_counter() - t0
         tot_bytes += m * RECORD
-    return {"value": round(tot_bytes / tot_s / 1e9, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {m:,} records of each of the two 100M-record key sets, oracle sort "
-                      f"(1024 partitions, 1% sample), single-threaded"}
+    out = {"value": round(tot_bytes / t_all / 1e9, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+           "cpu_model": cpu_model(),
+           "sample": f"first {m:,} records of each of the two 100M-record key sets, oracle sort (1024 partitions, "
+                     f"1% sample) with its classification and partition sorts spread over {cores} host threads"}
+    if single:
+        out["single_thread"] = {"value": round(tot_bytes / t_one / 1e9, 4), "cores": 1}
+    return out
 
 
 def dist_setup(args):
@@ -182,7 +241,7 @@ def run_reference(args):
     for _ in range(args.warmup):
         pass  # the oracle has no warm state; warm-up steps would only repeat the same CPU work
     t0 = time.perf_counter()
-    vals = [cpu_baseline(args) for _ in range(args.steps)]
+    vals = [cpu_baseline(args, single=False) for _ in range(args.steps)]
     dt = time.perf_counter() - t0
     v = statistics.mean(x["value"] for x in vals)
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
@@ -247,10 +306,13 @@ def run_elsar(args):
     peaks, how = measured_peaks()
     sg_ms = pass_ms[4]
     achieved = n * SORT_GATHER_BYTES / (sg_ms / 1e3) / 1e9
+    tpr, tsrc = profiled_traffic()
     roof = {"kernel": "sort_gather_kernel", "bound": "hbm", "achieved": round(achieved, 1),
             "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4),
             "peak_source": how,
-            "traffic": round(SORT_GATHER_TRAFFIC_PER_RECORD * n) if SORT_GATHER_TRAFFIC_PER_RECORD else None,
+            "traffic": round(tpr * n) if tpr else None,
+            "traffic_source": (f"ncu dram bytes per record {tpr} x {n} records, {TRAFFIC_PROFILE} (kernel digest "
+                               f"{tsrc})") if tpr else tsrc,
             "bytes_per_record": SORT_GATHER_BYTES, "avg_launch_ms": round(sg_ms, 3)}
 
     # plain form on the same data
@@ -293,7 +355,10 @@ def run_elsar(args):
         del ws, out
         torch.cuda.empty_cache()
         ooc = run_ooc(args, h_ins, h_out, n, dev, stream)
+    ins = out = ws = None  # the step's device buffers are not needed any more
+    torch.cuda.empty_cache()
     batched = None if args.no_batched else run_batched(args, dev, stream)
+    cfg4 = None if args.no_cfg4 else run_cfg4(args, dev, stream)
     if rank != 0:
         return
     cpu = cpu_baseline(args) if world == 1 and not args.no_cpu else None
@@ -307,7 +372,7 @@ def run_elsar(args):
         "records_per_s": round(world * len(workloads()) * n / (ms / 1e3)),
         "hbm_frac_200B": round(world * len(workloads()) * n * 200 / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "plain": plain, "batched": batched,
-        "ooc": ooc,
+        "ooc": ooc, "learned_500M": cfg4,
         "passes_ms": {"fit": round(pass_ms[0], 3), "classify": round(pass_ms[1], 3),
                       "scan_cuts_items": round(pass_ms[2], 3), "scatter": round(pass_ms[3], 3),
                       "sort_gather": round(sg_ms, 3)},
@@ -414,15 +479,74 @@ def run_batched(args, dev, stream):
     total = sum(sizes)
     info = b.info()
     b.close()
+    # once, outside the timed region: a spread of sets checked as sorted, stable
+    # permutations of their inputs (the checker of the full-size tests)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from stable_check import check_stable_sort
+
+    step = max(1, len(sizes) // args.batch_validate)
+    checked, valid = 0, True
+    for k in range(0, len(sizes), step):
+        try:
+            check_stable_sort(d_ins[k], d_outs[k], sizes[k])
+        except AssertionError:
+            valid = False
+        checked += 1
     del d_ins, d_outs
     torch.cuda.empty_cache()
     return {"value": round(total * RECORD / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "ms_per_run": round(ms, 3),
+            "validated_sets": checked, "valid": valid,
             "sets": len(sizes), "records": total, "graph_launches_per_run": 1,
             "kernels_in_graph": info["launches"], "tile_pairs": info["tile_pairs"],
             "records_per_bin_log2_by_class": info["records_per_bin_log2"], "autotune_runs": info["tuning_runs"],
             "plan_create_s": round(create_s, 2),
             "workload": "4096 sets, sizes log-uniform in [1K, 1M] records scaled to <= 4e8 records, "
                         "even sets uniform, odd sets Zipf(1.1) with 5% duplicates"}
+
+
+def run_cfg4(args, dev, stream):
+    """The learned model at scale: 500M records (Zipf 1.3 per byte, 10 % duplicate
+    keys), 4096 partitions, the network requested (its checks on) next to the
+    RMI alone.  Per model: GB/s of the default form (refined cuts), the model
+    that classified, the fallback reason, and the partition imbalance under both
+    cut rules."""
+    import torch
+
+    import paper_2305_05671_b300 as elsar
+    import recgen
+
+    wl = recgen.ZIPF13_500M
+    n, P = args.cfg4_records, wl["P"]
+    d_in = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
+    recgen.generate_gpu(d_in, n, wl["spec"], stream=stream.cuda_stream)
+    d_out = torch.empty_like(d_in)
+    res = {}
+    for name, kind in (("rmi", elsar.MODEL_RMI), ("network", elsar.MODEL_MLP)):
+        p = elsar.Params(num_partitions=P, seed=0x5EED, model_kind=kind)
+        ws = elsar.alloc_workspace(n, p, device=dev)
+        st = elsar.sort(d_in, d_out, n, p, ws=ws, stream=stream, stats=True)  # warm-up
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.cfg4_steps):
+            st = elsar.sort(d_in, d_out, n, p, ws=ws, stream=stream, stats=True)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1) / args.cfg4_steps
+        pp = elsar.Params(num_partitions=P, seed=0x5EED, model_kind=kind, balance=elsar.BALANCE_PAPER)
+        sp = elsar.sort(d_in, d_out, n, pp, ws=ws, stream=stream, stats=True)
+        torch.cuda.synchronize()
+        res[name] = {"value": round(n * RECORD / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "ms": round(ms, 3),
+                     "model_used": ["rmi", "network", "radix"][st["model_used"]],
+                     "fallback_reason": st["fallback_reason"], "fit_ms": round(st["pass_ms"][0], 3),
+                     "imbalance_refined": round(st["max_partition"] * P / n, 4),
+                     "imbalance_paper_rule": round(sp["max_partition"] * P / n, 4),
+                     "judge": {"buckets": st["judge_buckets"], "rmi_max": st["judge_rmi_max"],
+                               "network_max": st["judge_mlp_max"]} if kind == elsar.MODEL_MLP else None}
+        del ws
+        torch.cuda.empty_cache()
+    del d_in, d_out
+    torch.cuda.empty_cache()
+    return {"workload": f"{n:,} records (Zipf 1.3 per byte, 10% duplicates), {P} partitions", **res}
 
 
 def main():
@@ -444,6 +568,10 @@ def main():
     ap.add_argument("--no-ooc", action="store_true", help="skip the out-of-core measurement")
     ap.add_argument("--ooc-budget-gb", type=float, default=2.0, help="device budget of the out-of-core sort")
     ap.add_argument("--batch-cap", type=int, default=400_000_000, help="records across all batched sets")
+    ap.add_argument("--batch-validate", type=int, default=64, help="batched sets checked after the timed runs")
+    ap.add_argument("--no-cfg4", action="store_true", help="skip the 500M-record learned-model comparison")
+    ap.add_argument("--cfg4-records", type=int, default=500_000_000)
+    ap.add_argument("--cfg4-steps", type=int, default=2)
     args = ap.parse_args()
     global _SETS
     _SETS = tuple(args.sets.split(","))

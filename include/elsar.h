@@ -22,7 +22,10 @@
  *    aborts.  elsar_last_error() gives a message for the calling thread.
  *  - Supported: 0 <= n < 2^32 records.  Larger n returns ELSAR_EUNSUPPORTED.
  *  - The library allocates no device memory: scratch lives in the caller's
- *    workspace (size from elsar_workspace_size).
+ *    workspace (size from elsar_workspace_size).  The one exception is
+ *    elsar_sort_noalloc, whose scratch is a fixed array of
+ *    ELSAR_NOALLOC_SCRATCH_BYTES (16 MiB) compiled into the library, held on
+ *    every GPU that loads it until the process exits.
  */
 #ifndef ELSAR_H
 #define ELSAR_H
@@ -50,9 +53,19 @@ typedef enum elsar_status {
 } elsar_status;
 
 typedef enum elsar_model_kind {
-  ELSAR_MODEL_RMI = 0, /* the paper's RMI of linear models (Sec. 3.1) */
-  ELSAR_MODEL_MLP = 1  /* monotone MLP CDF trained on the GPU; the RMI is its fallback */
+  ELSAR_MODEL_RMI = 0,  /* the paper's RMI of linear models (Sec. 3.1) */
+  ELSAR_MODEL_MLP = 1,  /* monotone MLP CDF trained on the GPU; the RMI is its fallback */
+  ELSAR_MODEL_RADIX = 2 /* no model: equal-width slices of the printable key domain, the
+                           radix-based partitioning the paper compares with (Sec. 3, Sec. 3.3) */
 } elsar_model_kind;
+
+/* Checks that decide whether a requested network is used (model_kind MLP);
+ * skip_checks is an OR of the ones to leave out (0 = all three apply). */
+typedef enum elsar_check {
+  ELSAR_SKIP_BOUNDARY = 1, /* F of the smallest / largest sample key within 1/16 of 0 / 1 */
+  ELSAR_SKIP_JUDGE = 2,    /* held-out sample at least as balanced as under the RMI */
+  ELSAR_SKIP_IMBALANCE = 4 /* full-data largest partition at most 1.1 x the mean */
+} elsar_check;
 
 typedef enum elsar_balance {
   ELSAR_BALANCE_PAPER = 0,  /* partition p = min(P-1, floor(P * F(x)))  (Algorithm 1 reader loop) */
@@ -78,6 +91,14 @@ typedef struct elsar_params {
   uint32_t tile_pairs;     /* max pairs one CTA sorts in shared memory; 0 = tuned default */
   uint64_t sample_size;    /* S; 0 = 1% of n within [1000, 10^7] (Sec. 3.1, Sec. 6); must be < 2^24 */
   uint64_t seed;           /* seed of the key sample (SplitMix64 counter stream) */
+  uint32_t skip_checks;    /* OR of elsar_check values: network checks to leave out; default 0 */
+  uint32_t key_bytes;      /* l in [1, 10]: the key is the first l bytes of each record; 0 = 10.  Keys
+                              shorter than the longest (variable-length keys, Sec. 4) are padded with
+                              0 bytes, which sort below every printable character; the bytes after the
+                              first l are payload and are not compared. */
+  uint64_t wait_limit_cycles; /* limit of every device-side bounded wait of the bulk-copy pipelines
+                                 (classify, scatter), in SM clock cycles; 0 = 2e9 (about a second).
+                                 A wait that runs out makes the call return ELSAR_ETIMEOUT. */
 } elsar_params;
 
 /* Per-call measurements, filled when a non-NULL pointer is passed.  Passing
@@ -94,6 +115,10 @@ typedef struct elsar_stats {
   uint32_t fallback_reason; /* MLP asked for but not used: 1 boundary check (F of the smallest / largest
                                sample key not within 1/16 of 0 / 1), 2 less balanced than the RMI on a
                                held-out sample, 3 full-data partition imbalance above 1.1; 0 otherwise */
+  /* the network's checks (model_kind MLP; zero otherwise): the judge's J buckets, the held-out keys
+     in the largest bucket under the RMI and under the network, F at the first and last knot */
+  uint32_t judge_buckets, judge_rmi_max, judge_mlp_max, reserved;
+  float F_first_knot, F_last_knot;
 } elsar_stats;
 
 /* Fill *p with the defaults. */
@@ -252,14 +277,19 @@ void elsar_batch_destroy(elsar_batch* b);
  * (Sec. 3.1) is the RMI; its definition: 12 features of a key encoding x are
  * ramps between 13 sorted-sample knots T (phi_m = clamp(x - T_m, 0, W_m) / W_m
  * with W_m = T_{m+1} - T_m, formed exactly then scaled in FP64 and rounded to
- * FP32), two hidden layers of 32 with sigma(z) = 0.5 + 0.5 z / (1 + |z|),
- * F = clamp(output, 0, 1); weights are non-negative.  Parameters are 1505
- * floats laid out W1[32][12], b1[32], W2[32][32], b2[32], w3[32], b3.
+ * FP32), two hidden layers of 32 with sigma(z) = 0.5 + 0.5 z / (1 + |z|), an
+ * output z = b3 + sum_j w3_j h2_j + sum_m v_m phi_m (a linear skip from the
+ * features), F = clamp(z, 0, 1); all weights (W1, W2, w3, v) are
+ * non-negative, so F is monotone.  Parameters are 1517 floats laid out
+ * W1[32][12], b1[32], W2[32][32], b2[32], w3[32], b3, v[12].  Training starts
+ * from F = sum(phi) / 12 (the interpolation of the sample CDF between the
+ * knots) and takes 400 Adam steps on minibatches of 8192 sample keys, the
+ * learning rate decayed from 1e-3 to 1e-5 by a half cosine.
  *
- * elsar_mlp_eval: F of each key encoding, FP32 (d_w 1505 floats, d_knots 13
+ * elsar_mlp_eval: F of each key encoding, FP32 (d_w 1517 floats, d_knots 13
  *   u64, d_x n u64 encodings, d_F n floats).  Asynchronous.
  * elsar_mlp_grad: gradient of mean((F - y)^2) over n samples, FP32 with a
- *   fixed summation order (d_y n floats, d_grad 1505 floats); needs
+ *   fixed summation order (d_y n floats, d_grad 1517 floats); needs
  *   elsar_mlp_grad_workspace(n) bytes of scratch.  Asynchronous.
  * elsar_mlp_splitters: the 2^log2B fine-bin splitters of the network
  *   (t[0] = 0; t[q] = smallest encoding whose bin floor(2^log2B F) >= q, then
@@ -273,6 +303,17 @@ elsar_status elsar_mlp_grad(const float* d_w, const uint64_t* d_knots, const uin
                             uint64_t n, float* d_grad, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
 elsar_status elsar_mlp_splitters(const float* d_w, const uint64_t* d_knots, uint32_t log2B, uint64_t* d_t,
                                  elsar_stream_t stream);
+/*
+ * One Adam step of the network's training (Kingma & Ba 2015, Algorithm 1), as
+ * the trainer applies it, for parity checks: with step number t >= 1, the
+ * moments d_m and d_v (1517 floats each, updated in place) take the gradient
+ * d_grad (1517 floats), the bias-corrected step lr * mhat / (sqrt(vhat) + 1e-8)
+ * is subtracted from d_w, and the weights (not the biases) are projected onto
+ * >= 0.  Decay rates 0.9 and 0.999.  FP32.  Asynchronous.
+ * Errors: EINVAL (null pointers, t == 0); ECUDA.
+ */
+elsar_status elsar_mlp_adam(float* d_w, const float* d_grad, float* d_m, float* d_v, uint32_t t, float lr,
+                            elsar_stream_t stream);
 
 /* Bytes of the scratch area built into the library for elsar_sort_noalloc. */
 #define ELSAR_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -301,7 +342,6 @@ elsar_status elsar_mlp_splitters(const float* d_w, const uint64_t* d_knots, uint
 elsar_status elsar_sort_noalloc(const void* d_in, void* d_out, uint64_t n, const elsar_params* p,
                                 elsar_stream_t stream);
 
-/* Static description of a status code. */
 /*
  * Failure-detection self-test of the bounded waits that guard every TMA
  * pipeline: one CTA waits on an mbarrier phase that nothing completes while
@@ -318,6 +358,7 @@ elsar_status elsar_sort_noalloc(const void* d_in, void* d_out, uint64_t n, const
 elsar_status elsar_selftest_bounded_wait(const void* d_src, void* d_word, uint64_t limit_cycles,
                                          elsar_stream_t stream, uint32_t* h_result);
 
+/* Static description of a status code. */
 const char* elsar_status_str(elsar_status s);
 
 /* Message of the last failing call on this thread ("" if none). */

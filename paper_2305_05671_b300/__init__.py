@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libelsar.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "elsar.h")
 RECORD = 100
 
-MODEL_RMI, MODEL_MLP = 0, 1
+MODEL_RMI, MODEL_MLP, MODEL_RADIX = 0, 1, 2
+SKIP_BOUNDARY, SKIP_JUDGE, SKIP_IMBALANCE = 1, 2, 4
 BALANCE_PAPER, BALANCE_REFINED = 0, 1
 SCHED_PER_PARTITION, SCHED_PERSISTENT = 0, 1
 
@@ -31,14 +32,17 @@ class _Params(ctypes.Structure):
     _fields_ = [("num_partitions", ctypes.c_uint32), ("fine_bins_log2", ctypes.c_uint32),
                 ("leaf_target", ctypes.c_uint32), ("max_depth", ctypes.c_uint32), ("model_kind", ctypes.c_uint32),
                 ("balance", ctypes.c_uint32), ("schedule", ctypes.c_uint32), ("tile_pairs", ctypes.c_uint32),
-                ("sample_size", ctypes.c_uint64), ("seed", ctypes.c_uint64)]
+                ("sample_size", ctypes.c_uint64), ("seed", ctypes.c_uint64), ("skip_checks", ctypes.c_uint32),
+                ("key_bytes", ctypes.c_uint32), ("wait_limit_cycles", ctypes.c_uint64)]
 
 
 class _Stats(ctypes.Structure):
     _fields_ = [("pass_ms", ctypes.c_float * 8), ("launches", ctypes.c_uint32), ("num_items", ctypes.c_uint32),
                 ("oversize_items", ctypes.c_uint32), ("model_nodes", ctypes.c_uint32),
                 ("max_partition", ctypes.c_uint64), ("max_bin", ctypes.c_uint64), ("model_used", ctypes.c_uint32),
-                ("fallback_reason", ctypes.c_uint32)]
+                ("fallback_reason", ctypes.c_uint32), ("judge_buckets", ctypes.c_uint32),
+                ("judge_rmi_max", ctypes.c_uint32), ("judge_mlp_max", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("F_first_knot", ctypes.c_float), ("F_last_knot", ctypes.c_float)]
 
 
 class _BatchInfo(ctypes.Structure):
@@ -68,6 +72,9 @@ class Params:
     tile_pairs: int = 0
     sample_size: int = 0
     seed: int = 0x5EED
+    skip_checks: int = 0
+    key_bytes: int = 0
+    wait_limit_cycles: int = 0
 
     def c(self) -> _Params:
         return _Params(*[getattr(self, f.name) for f in fields(self)])
@@ -102,6 +109,7 @@ def lib():
             "elsar_mlp_eval": (ctypes.c_int, [P, P, P, U64, P, P]),
             "elsar_mlp_grad": (ctypes.c_int, [P, P, P, P, U64, P, P, SZ, P]),
             "elsar_mlp_splitters": (ctypes.c_int, [P, P, ctypes.c_uint32, P, P]),
+            "elsar_mlp_adam": (ctypes.c_int, [P, P, P, P, ctypes.c_uint32, ctypes.c_float, P]),
             "elsar_batch_workspace_size": (SZ, [P, ctypes.c_uint32, PP]),
             "elsar_batch_create": (ctypes.c_int, [P, P, P, ctypes.c_uint32, PP, P, SZ, P, ctypes.POINTER(P)]),
             "elsar_batch_run": (ctypes.c_int, [P, P]),
@@ -198,7 +206,9 @@ def sort(d_in, d_out, n: int, p: Params | None = None, ws=None, stream=None, sta
         return None
     return dict(pass_ms=list(st.pass_ms)[:5], launches=st.launches, num_items=st.num_items,
                 oversize_items=st.oversize_items, model_nodes=st.model_nodes, max_partition=st.max_partition,
-                max_bin=st.max_bin, model_used=st.model_used, fallback_reason=st.fallback_reason)
+                max_bin=st.max_bin, model_used=st.model_used, fallback_reason=st.fallback_reason,
+                judge_buckets=st.judge_buckets, judge_rmi_max=st.judge_rmi_max, judge_mlp_max=st.judge_mlp_max,
+                F_first_knot=st.F_first_knot, F_last_knot=st.F_last_knot)
 
 
 def sort_noalloc(d_in, d_out, n: int, p: Params | None = None, stream=None):
@@ -254,6 +264,11 @@ def mlp_grad(d_w, d_knots, d_x, d_y, n: int, d_grad, stream=None):
                                 _nbytes(ws), _stream(stream)))
 
 
+def mlp_adam(d_w, d_grad, d_m, d_v, t: int, lr: float = 1e-3, stream=None):
+    """One Adam step of the trainer (in place on d_w, d_m, d_v)."""
+    _check(lib().elsar_mlp_adam(_ptr(d_w), _ptr(d_grad), _ptr(d_m), _ptr(d_v), t, lr, _stream(stream)))
+
+
 def mlp_splitters(d_w, d_knots, log2B: int, d_t, stream=None):
     _check(lib().elsar_mlp_splitters(_ptr(d_w), _ptr(d_knots), log2B, _ptr(d_t), _stream(stream)))
 
@@ -305,6 +320,7 @@ class Batch:
 
 
 # ---- device model buffer layout (read back for inspection and parity tests)
+MLP_PARAMS = 1517  # the network's parameters (include/elsar.h gives the layout)
 MODEL_HEADER_BYTES = 256
 NODE_BYTES = 64
 
@@ -329,5 +345,5 @@ def read_model(d_model, p: Params, n: int):
     h = {k: hdr[k].item() for k in hdr.dtype.names}
     ko, wo = int(hdr["knots_off"]), int(hdr["weights_off"])
     h["mlp_knots"] = np.frombuffer(buf[ko:ko + 104].tobytes(), dtype=np.uint64).copy()
-    h["mlp_w"] = np.frombuffer(buf[wo:wo + 1505 * 4].tobytes(), dtype=np.float32).copy()
+    h["mlp_w"] = np.frombuffer(buf[wo:wo + MLP_PARAMS * 4].tobytes(), dtype=np.float32).copy()
     return h, nodes, spl

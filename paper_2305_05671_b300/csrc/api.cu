@@ -37,8 +37,9 @@ elsar_status cuda_fail(cudaError_t e, const char* where) {
 }
 
 struct Resolved {
-  uint32_t P, log2B, T, Dmax, kind, balance, schedule, cap;
+  uint32_t P, log2B, T, Dmax, kind, balance, schedule, cap, skip, key_bytes;
   uint64_t S, seed;
+  long long wait_limit;
 };
 
 uint32_t ilog2(uint64_t v) {
@@ -70,7 +71,13 @@ elsar_status resolve(uint64_t n, const elsar_params* p, Resolved* r) {
   r->T = q.leaf_target ? q.leaf_target : 16;
   r->Dmax = q.max_depth ? q.max_depth : 32;
   r->kind = q.model_kind;
-  if (r->kind > 1) return fail(ELSAR_EINVAL, "unknown model_kind");
+  if (r->kind > 2) return fail(ELSAR_EINVAL, "unknown model_kind");
+  r->skip = q.skip_checks;
+  if (r->skip > 7) return fail(ELSAR_EINVAL, "skip_checks must be an OR of ELSAR_SKIP_* values");
+  r->key_bytes = q.key_bytes ? q.key_bytes : 10;
+  if (r->key_bytes > 10) return fail(ELSAR_EINVAL, "key_bytes must be in [1, 10] (0 = 10)");
+  if (q.wait_limit_cycles > (1ull << 40)) return fail(ELSAR_EINVAL, "wait_limit_cycles must be <= 2^40");
+  r->wait_limit = q.wait_limit_cycles ? (long long)q.wait_limit_cycles : kWaitLimitCycles;
   r->balance = q.balance;
   if (r->balance > 1) return fail(ELSAR_EINVAL, "unknown balance rule");
   r->schedule = q.schedule;
@@ -96,7 +103,8 @@ struct Layout {
 };
 
 constexpr uint64_t kMlpTrainMax = 2000000;  // keys the network trains on (every k-th of the sorted sample)
-constexpr uint32_t kMlpBatch = 65536, kMlpEpochs = 20, kMlpGrid = 512;
+constexpr uint32_t kMlpBatch = 8192, kMlpSteps = 400, kMlpGrid = 512;
+constexpr float kMlpLr = 1e-3f, kMlpLrMin = 1e-5f;
 
 uint64_t mlp_ntrain(uint64_t S) { return S < kMlpTrainMax ? S : kMlpTrainMax; }
 
@@ -137,7 +145,7 @@ Layout layout(uint64_t n, const Resolved& r) {
   L.mlp_m = take(mlp ? kMlpParamCount * 4 : 0);
   L.mlp_v = take(mlp ? kMlpParamCount * 4 : 0);
   L.swap = take(mlp ? B * 8 : 0);
-  L.judge = take(mlp ? B * 8 : 0);
+  L.judge = take(mlp ? (2 * B + 13) * 4 : 0);  // two J-bucket histograms (J <= B) and F at the 13 knots
   L.total = o;
   return L;
 }
@@ -168,20 +176,22 @@ const uint32_t* lut_in(const void* d_model, const Resolved& r) {
 
 struct FitResult {
   uint32_t nodes = 0, kind = ELSAR_MODEL_RMI, fallback = 0;
+  uint32_t judge_J = 0, judge_rmi_max = 0, judge_mlp_max = 0;
+  float F_first = 0.0f, F_last = 0.0f;
 };
 
-// max / mean of a judge histogram (J buckets)
-double max_over_mean(const std::string& h, uint32_t J, uint64_t total) {
-  const uint32_t* c = reinterpret_cast<const uint32_t*>(h.data());
+// largest count of a judge histogram (J buckets)
+uint32_t max_bucket(const uint32_t* c, uint32_t J) {
   uint32_t mx = 0;
   for (uint32_t j = 0; j < J; ++j) mx = c[j] > mx ? c[j] : mx;
-  return total ? (double)mx * J / (double)total : 0.0;
+  return mx;
 }
 
 elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* d_model, void* d_ws, const Layout& L,
                     cudaStream_t st, uint32_t* launches, FitResult* res) {
   FitArgs f = {};
   f.records = static_cast<const uint8_t*>(d_records);
+  f.km = key_mask(r.key_bytes);
   f.n = n;
   f.S = r.S;
   f.seed = r.seed;
@@ -198,8 +208,16 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
   f.sets = at<SetInfo>(d_ws, L.sets);
   f.stream = st;
   f.launches = launches;
+  cudaError_t e;
+  if (r.kind == ELSAR_MODEL_RADIX) {  // no model to fit: equal-width slices
+    if ((e = fit_radix(f)) != cudaSuccess) return cuda_fail(e, "radix");
+    res->kind = ELSAR_MODEL_RADIX;
+    res->fallback = 0;
+    res->nodes = 0;
+    return ELSAR_OK;
+  }
   const uint64_t* sorted = nullptr;
-  cudaError_t e = fit_rmi(f, &res->nodes, &sorted);
+  e = fit_rmi(f, &res->nodes, &sorted);
   if (e != cudaSuccess) return cuda_fail(e, "fit");
   res->kind = ELSAR_MODEL_RMI;
   res->fallback = 0;
@@ -216,8 +234,9 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
   ta.S = r.S;
   ta.ntrain = mlp_ntrain(r.S);
   ta.batch = kMlpBatch;
-  ta.epochs = kMlpEpochs;
-  ta.lr = 1e-3f;
+  ta.steps = kMlpSteps;
+  ta.lr = kMlpLr;
+  ta.lr_min = kMlpLrMin;
   ta.T = T;
   ta.w = w;
   ta.m = at<float>(d_ws, L.mlp_m);
@@ -236,23 +255,27 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
   while (log2J < r.log2B && (64ull << (log2J + 1)) <= r.S) ++log2J;
   const uint32_t J = 1u << log2J;
   uint32_t* hj = at<uint32_t>(d_ws, L.judge);
-  if ((e = sample_keys(f.records, n, r.S, r.seed + 1, held, st)) != cudaSuccess) return cuda_fail(e, "held-out");
+  if ((e = sample_keys(f.records, n, r.S, r.seed + 1, f.km, held, st)) != cudaSuccess) return cuda_fail(e, "held-out");
   if ((e = judge_histogram(held, r.S, rmi_t, r.log2B, log2J, hj, st)) != cudaSuccess) return cuda_fail(e, "judge");
   if ((e = judge_histogram(held, r.S, mlp_t, r.log2B, log2J, hj + J, st)) != cudaSuccess) return cuda_fail(e, "judge");
   // boundary check: F at the smallest and largest sample keys
   float* Fb = reinterpret_cast<float*>(hj + 2 * J);
   if ((e = mlp_eval(w, T, T, 13, Fb, st)) != cudaSuccess) return cuda_fail(e, "mlp eval");
-  std::string hh((size_t)2 * J * 4 + 13 * 4, '\0');
-  e = cudaMemcpyAsync(&hh[0], hj, hh.size(), cudaMemcpyDeviceToHost, st);
+  std::vector<uint32_t> hh((size_t)2 * J + 13);
+  e = cudaMemcpyAsync(hh.data(), hj, hh.size() * 4, cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "judge readback");
-  const double rmi_mm = max_over_mean(hh.substr(0, (size_t)J * 4), J, r.S);
-  const double mlp_mm = max_over_mean(hh.substr((size_t)J * 4, (size_t)J * 4), J, r.S);
-  const float* Fk = reinterpret_cast<const float*>(hh.data() + (size_t)2 * J * 4);
+  res->judge_J = J;
+  res->judge_rmi_max = max_bucket(hh.data(), J);
+  res->judge_mlp_max = max_bucket(hh.data() + J, J);
+  float Fk[13];
+  std::memcpy(Fk, hh.data() + 2 * J, sizeof Fk);
+  res->F_first = Fk[0];
+  res->F_last = Fk[12];
   // coarse sanity of the ends (the held-out balance below judges the rest)
   const bool boundary_ok = Fk[0] < 1.0f / 16 && Fk[12] > 1.0f - 1.0f / 16;
-  if (!boundary_ok) res->fallback = 1;
-  else if (mlp_mm > rmi_mm) res->fallback = 2;
+  if (!(r.skip & ELSAR_SKIP_BOUNDARY) && !boundary_ok) res->fallback = 1;
+  else if (!(r.skip & ELSAR_SKIP_JUDGE) && res->judge_mlp_max > res->judge_rmi_max) res->fallback = 2;
   if (res->fallback == 0) {
     // the network wins: its splitters become the active ones, the RMI's are kept as the alternate
     uint64_t* tmp = at<uint64_t>(d_ws, L.swap);
@@ -288,6 +311,7 @@ PartArgs part_args(const void* d_model, const void* d_records, uint64_t n, const
                    uint32_t* launches) {
   PartArgs a = {};
   a.records = static_cast<const uint8_t*>(d_records);
+  a.km = key_mask(r.key_bytes);
   a.n = n;
   a.splitters = splitters_in(d_model, r);
   a.lut = lut_in(d_model, r);
@@ -307,6 +331,7 @@ PartArgs part_args(const void* d_model, const void* d_records, uint64_t n, const
   a.ctrl = at<uint32_t>(d_ws, L.ctrl);
   a.seg_hist = at<uint32_t>(d_ws, L.seg);
   a.mid = at<void>(d_ws, L.pairsB);
+  a.wait_limit = r.wait_limit;
   a.stream = st;
   a.launches = launches;
   return a;
@@ -485,20 +510,22 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
     a.ev[2] = ev[4];
     cudaError_t e = partition_records(a);
     if (e != cudaSuccess) s = cuda_fail(e, "partition");
-    if (s == ELSAR_OK && fr.kind == ELSAR_MODEL_MLP) {
+    if (s == ELSAR_OK && fr.kind == ELSAR_MODEL_MLP && !(r.skip & ELSAR_SKIP_IMBALANCE)) {
       // full-data check of the network's partitions: above 1.1 x the mean, the RMI takes over
-      std::string po((r.P + 1) * 8, '\0');
-      e = cudaMemcpyAsync(&po[0], at<uint64_t>(d_ws, L.part_off), po.size(), cudaMemcpyDeviceToHost, st);
+      std::vector<uint64_t> off(r.P + 1);
+      e = cudaMemcpyAsync(off.data(), at<uint64_t>(d_ws, L.part_off), off.size() * 8, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-      if (e != cudaSuccess) return cuda_fail(e, "partition readback");
-      const uint64_t* off = reinterpret_cast<const uint64_t*>(po.data());
-      uint64_t mx = 0;
-      for (uint32_t q = 0; q < r.P; ++q) mx = off[q + 1] - off[q] > mx ? off[q + 1] - off[q] : mx;
-      if ((double)mx * r.P > 1.1 * (double)n) {
-        fr.kind = ELSAR_MODEL_RMI;
-        fr.fallback = 3;
-        s = revert_to_rmi(model, r, d_ws, L, st, 3);
-        if (s == ELSAR_OK && (e = partition_records(a)) != cudaSuccess) s = cuda_fail(e, "partition");
+      if (e != cudaSuccess) {
+        s = cuda_fail(e, "partition readback");
+      } else {
+        uint64_t mx = 0;
+        for (uint32_t q = 0; q < r.P; ++q) mx = off[q + 1] - off[q] > mx ? off[q + 1] - off[q] : mx;
+        if ((double)mx * r.P > 1.1 * (double)n) {
+          fr.kind = ELSAR_MODEL_RMI;
+          fr.fallback = 3;
+          s = revert_to_rmi(model, r, d_ws, L, st, 3);
+          if (s == ELSAR_OK && (e = partition_records(a)) != cudaSuccess) s = cuda_fail(e, "partition");
+        }
       }
     }
   }
@@ -526,6 +553,11 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
       stats->model_nodes = fr.nodes;
       stats->model_used = fr.kind;
       stats->fallback_reason = fr.fallback;
+      stats->judge_buckets = fr.judge_J;
+      stats->judge_rmi_max = fr.judge_rmi_max;
+      stats->judge_mlp_max = fr.judge_mlp_max;
+      stats->F_first_knot = fr.F_first;
+      stats->F_last_knot = fr.F_last;
       uint32_t c[4];
       cudaMemcpy(c, at<uint32_t>(d_ws, L.ctrl), sizeof c, cudaMemcpyDeviceToHost);
       stats->num_items = c[kNumItems];
@@ -782,7 +814,7 @@ extern "C" elsar_status elsar_sort_ooc(const void* h_in, void* h_out, uint64_t n
       if ((s = device_status(d_ws, Lf, st)) != ELSAR_OK) break;  // a classify wait gave up
       uint64_t mx = 0;
       for (uint32_t q = 0; q < r.P; ++q) mx = std::max<uint64_t>(mx, part_off[q + 1] - part_off[q]);
-      if (fr.kind == ELSAR_MODEL_MLP && (double)mx * r.P > 1.1 * (double)n) {
+      if (fr.kind == ELSAR_MODEL_MLP && !(r.skip & ELSAR_SKIP_IMBALANCE) && (double)mx * r.P > 1.1 * (double)n) {
         fr.kind = ELSAR_MODEL_RMI;
         fr.fallback = 3;
         s = revert_to_rmi(model, r, d_ws, Lf, st, 3);
@@ -922,6 +954,15 @@ elsar_status elsar_mlp_grad(const float* d_w, const uint64_t* d_knots, const uin
   float* partial = at<float>(d_ws, (n * 12 * 4 + 255) & ~(size_t)255);
   cudaError_t e = mlp_grad(d_w, d_knots, d_x, d_y, n, phi, partial, kMlpGrid, d_grad, (cudaStream_t)stream);
   return e == cudaSuccess ? ELSAR_OK : cuda_fail(e, "mlp grad");
+}
+
+elsar_status elsar_mlp_adam(float* d_w, const float* d_grad, float* d_m, float* d_v, uint32_t t, float lr,
+                            elsar_stream_t stream) {
+  g_err.clear();
+  if (!d_w || !d_grad || !d_m || !d_v) return fail(ELSAR_EINVAL, "null buffer");
+  if (t == 0) return fail(ELSAR_EINVAL, "the step number t starts at 1");
+  cudaError_t e = mlp_adam_step(d_w, d_grad, d_m, d_v, t, lr, (cudaStream_t)stream);
+  return e == cudaSuccess ? ELSAR_OK : cuda_fail(e, "mlp adam");
 }
 
 elsar_status elsar_mlp_splitters(const float* d_w, const uint64_t* d_knots, uint32_t log2B, uint64_t* d_t,

@@ -41,7 +41,7 @@ __device__ __forceinline__ uint32_t seg_of(const SetInfo* __restrict__ sets, uin
 }
 
 // sample j of the concatenation: set k, position mulhi64(SplitMix64_j'(seed + k), n_k)
-__global__ void batch_sample_kernel(const uint8_t* const* __restrict__ ins, const uint64_t* __restrict__ n,
+__global__ void batch_sample_kernel(const uint8_t* const* __restrict__ ins, KeyMask km, const uint64_t* __restrict__ n,
                                     const SetInfo* __restrict__ sets, uint32_t K, uint64_t S_total, uint64_t seed,
                                     Pair* __restrict__ out) {
   for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < S_total; j += (uint64_t)gridDim.x * blockDim.x) {
@@ -49,7 +49,7 @@ __global__ void batch_sample_kernel(const uint8_t* const* __restrict__ ins, cons
     const uint64_t i = __umul64hi(splitmix64_at(seed + k, j - sets[k].soff), n[k]);
     Pair p;
     p.hi = k;
-    p.lo = enc9_pair(load_pair(ins[k] + i * kRecord, 0));
+    p.lo = enc9_pair(load_pair(ins[k] + i * kRecord, 0, km));
     out[j] = p;
   }
 }
@@ -324,7 +324,8 @@ cudaError_t enqueue(elsar_batch& b, cudaStream_t st) {
   Pair* sp1 = at<Pair>(ws, L.sp1);
   const uint64_t S = L.S_total;
   batch_sample_kernel<<<(unsigned)umin64((S + 255) / 256 + 1, (uint64_t)sms * 8), 256, 0, st>>>(
-      at<const uint8_t* const>(ws, L.ins), at<uint64_t>(ws, L.n), at<SetInfo>(ws, L.sets), K, S, b.p.seed, sp0);
+      at<const uint8_t* const>(ws, L.ins), key_mask(b.p.key_bytes ? b.p.key_bytes : 10), at<uint64_t>(ws, L.n),
+      at<SetInfo>(ws, L.sets), K, S, b.p.seed, sp0);
   chunk_sort_pairs<<<(unsigned)((S + kChunk - 1) / kChunk), kChunkThreads, 0, st>>>(sp0, S);
   launches += 2;
   Pair* src = sp0;
@@ -368,6 +369,7 @@ cudaError_t enqueue(elsar_batch& b, cudaStream_t st) {
   // 4. classify, scan, scatter, work items
   BatchPartArgs pa = {};
   pa.ins = at<const uint8_t* const>(ws, L.ins);
+  pa.km = key_mask(b.p.key_bytes ? b.p.key_bytes : 10);
   pa.poff = at<uint64_t>(ws, L.poff);
   pa.K = K;
   pa.B = (uint32_t)L.B_total;
@@ -492,6 +494,10 @@ elsar_status elsar_batch_create(const void* const* d_in, void* const* d_out, con
   }
   if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255)) {
     set_last_error("elsar_batch_create: workspace must be non-null and 256-byte aligned");
+    return ELSAR_EINVAL;
+  }
+  if (p && p->key_bytes > 10) {
+    set_last_error("elsar_batch_create: key_bytes must be in [1, 10] (0 = 10)");
     return ELSAR_EINVAL;
   }
   uint64_t total = 0;

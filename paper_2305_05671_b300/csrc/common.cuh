@@ -91,15 +91,31 @@ __device__ __forceinline__ uint64_t enc9_pair(const Pair& p) {
   return enc9_words((uint32_t)(p.hi >> 32), (uint32_t)p.hi, (uint32_t)(p.lo >> 40) & 0xFFu);
 }
 
-// Load the 10-byte key of a 4-byte-aligned record and pack it.
-__device__ __forceinline__ Pair load_pair(const uint8_t* rec, uint32_t idx) {
+// Keys of key_bytes = l (1..10) bytes (Sec. 4's variable-length keys, l the
+// longest): the bytes of the key field after the key count as 0 -- in the
+// pair they are masked to 0, so the encoding saturates to 0 there and byte
+// order compares the padded keys.  hi keeps key bytes 0-7, lo bits 32-47
+// bytes 8-9 (and the record index below).
+struct KeyMask {
+  uint64_t hi, lo;
+};
+inline KeyMask key_mask(uint32_t key_bytes) {
+  KeyMask m;
+  m.hi = key_bytes >= 8 ? ~0ull : (key_bytes ? ~0ull << (64 - 8 * key_bytes) : 0ull);
+  const uint64_t lo16 = key_bytes >= 10 ? 0xFFFFull : (key_bytes == 9 ? 0xFF00ull : 0ull);
+  m.lo = (lo16 << 32) | 0xFFFFFFFFull;
+  return m;
+}
+
+// Load the key of a 4-byte-aligned record and pack it.
+__device__ __forceinline__ Pair load_pair(const uint8_t* rec, uint32_t idx, const KeyMask& km) {
   const uint32_t* w = reinterpret_cast<const uint32_t*>(rec);
   uint32_t a = __ldg(w), b = __ldg(w + 1), c = __ldg(w + 2);
   uint32_t be0 = __byte_perm(a, 0, 0x0123), be1 = __byte_perm(b, 0, 0x0123);
   uint32_t be16 = __byte_perm(c, 0, 0x4401);
   Pair p;
-  p.hi = ((uint64_t)be0 << 32) | be1;
-  p.lo = ((uint64_t)be16 << 32) | idx;
+  p.hi = (((uint64_t)be0 << 32) | be1) & km.hi;
+  p.lo = (((uint64_t)be16 << 32) | idx) & km.lo;
   return p;
 }
 
@@ -199,19 +215,41 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Bounded wait on an mbarrier phase: false after `limit` clock cycles.
+// Non-blocking test of an mbarrier phase (mbarrier.test_wait returns at once).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr long long kWaitLimitCycles = 2000000000ll;  // about one second at B300 clocks
+constexpr long long kShortWaitCycles = 1000000ll;     // limits below this poll without suspending
+
+// Bounded wait on an mbarrier phase: false after `limit` clock cycles.  A
+// try_wait may suspend the thread until the phase completes, so a short limit
+// (below kShortWaitCycles, about half a millisecond) polls with the
+// non-blocking test_wait instead, which lets it run out while a copy is
+// still in flight.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long limit) {
   const long long t0 = clock64();
+  if (limit < kShortWaitCycles) {
+    while (!mbar_test_wait(bar, parity))
+      if (clock64() - t0 > limit) return false;
+    return true;
+  }
   while (!mbar_try_wait(bar, parity))
     if (clock64() - t0 > limit) return false;
   return true;
 }
 
-constexpr long long kWaitLimitCycles = 2000000000ll;  // about one second at B300 clocks
-
 // ---------------------------------------------------------------- launchers
 struct FitArgs {
   const uint8_t* records;
+  KeyMask km;
   uint64_t n, S, seed;
   uint32_t log2B, T, Dmax;
   void* model;
@@ -262,13 +300,17 @@ inline size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T) { return m
 
 // fits the RMI; *sorted_out = the buffer holding the sorted sample (a.samp or a.samp + S)
 cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sorted_out);
-cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, uint64_t* out, cudaStream_t st);
+cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, const KeyMask& km, uint64_t* out,
+                        cudaStream_t st);
 // builds both levels of the radix index (scratch: kFineLutCells words)
 cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* lut, cudaStream_t st);
 cudaError_t set_model_kind(void* model, uint32_t kind, uint32_t fallback, cudaStream_t st);
+// no model: the equal-width (radix) splitters t_q = ceil(q 95^9 / B), their index and the header
+cudaError_t fit_radix(const FitArgs& a);
 
 struct PartArgs {
   const uint8_t* records;
+  KeyMask km;
   uint64_t n;
   const uint64_t* splitters;  // B fine-bin splitters of the fitted model
   const uint32_t* lut;        // radix index of the splitters
@@ -285,6 +327,7 @@ struct PartArgs {
   uint32_t* ctrl;        // control words
   void* mid;             // n pairs (scratch, 16-byte aligned): coarse-bin order between the two scatter passes
   uint32_t* seg_hist;    // coarse_segments(n) x kMaxCoarse counts of every classify CTA
+  long long wait_limit;  // limit of the bounded mbarrier waits (SM clock cycles)
   cudaStream_t stream;
   uint32_t* launches;
   cudaEvent_t ev[4];  // optional: after classify, after scan/cuts/items, after scatter
@@ -309,6 +352,7 @@ cudaError_t build_items(const PartArgs& a);
 // owning bins [tbase[k], tbase[k] + 2^log2B[k]) and pair slots [poff[k], poff[k+1])
 struct BatchPartArgs {
   const uint8_t* const* ins;  // device array of K record buffers
+  KeyMask km;
   const uint64_t* poff;       // K+1
   uint32_t K, B, tile_pairs;  // B = total bins
   const uint64_t* splitters;  // B

@@ -6,6 +6,7 @@
 // -fmad=false), so the fitted model is bit-identical wherever it is computed
 // in that order.  Least-squares sums are exact integers (order independent).
 #include "common.cuh"
+#include "mlp.cuh"
 
 namespace elsar {
 namespace {
@@ -62,11 +63,11 @@ __device__ __forceinline__ u128 shfl_down_u128(u128 v, int d) {
 }
 
 // ------------------------------------------------------------------ sample
-__global__ void sample_kernel(const uint8_t* __restrict__ rec, uint64_t n, uint64_t S, uint64_t seed,
+__global__ void sample_kernel(const uint8_t* __restrict__ rec, uint64_t n, uint64_t S, uint64_t seed, KeyMask km,
                               uint64_t* __restrict__ out) {
   for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < S; k += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t i = __umul64hi(splitmix64_at(seed, k), n);
-    out[k] = enc9_pair(load_pair(rec + i * kRecord, 0));
+    out[k] = enc9_pair(load_pair(rec + i * kRecord, 0, km));
   }
 }
 
@@ -619,6 +620,13 @@ __global__ void lut_fill_kernel(const uint64_t* __restrict__ t, const uint4* __r
   }
 }
 
+// equal-width slices of the printable key domain: t_q = ceil(q * 95^9 / B)
+__global__ void radix_splitter_kernel(uint32_t log2B, uint64_t* __restrict__ t) {
+  const uint32_t B = 1u << log2B;
+  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < B; q += gridDim.x * blockDim.x)
+    t[q] = (uint64_t)(((unsigned __int128)q * kEncTop + (B - 1)) >> log2B);
+}
+
 __global__ void set_single_kernel(SetInfo* sets, uint64_t S) {
   sets[0].soff = 0;
   sets[0].S = S;
@@ -646,7 +654,7 @@ ModelLayout model_layout(uint64_t S, uint32_t log2B, uint32_t T) {
   L.mlp_knots = o;
   o += 256;
   L.mlp_w = o;
-  o += up(1505 * 4);
+  o += up(kMlpParamCount * 4);
   L.alt_splitters = o;
   o += up((size_t)8 << log2B);
   L.bytes = o;
@@ -663,9 +671,37 @@ cudaError_t set_model_kind(void* model, uint32_t kind, uint32_t fallback, cudaSt
   return cudaGetLastError();
 }
 
-cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, uint64_t* out, cudaStream_t st) {
+cudaError_t fit_radix(const FitArgs& a) {
+  ModelHeader h = {};
+  h.magic = kModelMagic;
+  h.kind = 2;  // ELSAR_MODEL_RADIX
+  h.log2B = a.log2B;
+  h.S = a.S;
+  h.node_cap = node_cap_for(a.S, a.T);
+  const ModelLayout ml = model_layout(a.S, a.log2B, a.T);
+  h.nodes_off = ml.nodes;
+  h.splitters_off = ml.splitters;
+  h.bytes = ml.bytes;
+  h.lut_off = ml.lut;
+  h.knots_off = ml.mlp_knots;
+  h.weights_off = ml.mlp_w;
+  h.T = a.T;
+  h.Dmax = a.Dmax;
+  uint8_t* mb = static_cast<uint8_t*>(a.model);
+  uint64_t* t = reinterpret_cast<uint64_t*>(mb + ml.splitters);
+  const uint32_t B = 1u << a.log2B;
+  radix_splitter_kernel<<<(B + 255) / 256, 256, 0, a.stream>>>(a.log2B, t);
+  build_fine_lut(t, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut), a.stream);
+  cudaMemsetAsync(a.ctrl + kLevelNodes + 3, 0, 4, a.stream);  // no RMI nodes
+  write_header<<<1, 1, 0, a.stream>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
+  *a.launches += 6;
+  return cudaGetLastError();
+}
+
+cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, const KeyMask& km, uint64_t* out,
+                        cudaStream_t st) {
   const unsigned grid = (unsigned)umin64((S + 255) / 256, (uint64_t)sm_count() * 8);
-  sample_kernel<<<grid ? grid : 1, 256, 0, st>>>(records, n, S, seed, out);
+  sample_kernel<<<grid ? grid : 1, 256, 0, st>>>(records, n, S, seed, km, out);
   return cudaGetLastError();
 }
 
@@ -760,7 +796,7 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sort
   uint32_t& L = *a.launches;
   // 1. sample (Sec. 3.1)
   const unsigned sgrid = (unsigned)umin64((S + 255) / 256, (uint64_t)sms * 8);
-  sample_kernel<<<sgrid, 256, 0, st>>>(a.records, a.n, S, a.seed, a.samp);
+  sample_kernel<<<sgrid, 256, 0, st>>>(a.records, a.n, S, a.seed, a.km, a.samp);
   ++L;
   // 2. sort the sample
   chunk_sort_u64<<<(unsigned)((S + kChunk - 1) / kChunk), kChunkThreads, 0, st>>>(a.samp, S);

@@ -27,10 +27,10 @@ __device__ __forceinline__ uint32_t classify_one(const Pair& key, uint64_t i, co
   return q;
 }
 
-__device__ __forceinline__ Pair pair_from_words(uint32_t a, uint32_t b, uint32_t c) {
+__device__ __forceinline__ Pair pair_from_words(uint32_t a, uint32_t b, uint32_t c, const KeyMask& km) {
   Pair p;
-  p.hi = ((uint64_t)__byte_perm(a, 0, 0x0123) << 32) | __byte_perm(b, 0, 0x0123);
-  p.lo = (uint64_t)__byte_perm(c, 0, 0x4401) << 32;
+  p.hi = (((uint64_t)__byte_perm(a, 0, 0x0123) << 32) | __byte_perm(b, 0, 0x0123)) & km.hi;
+  p.lo = ((uint64_t)__byte_perm(c, 0, 0x4401) << 32) & km.lo;
   return p;
 }
 
@@ -45,11 +45,12 @@ __device__ __forceinline__ Pair pair_from_words(uint32_t a, uint32_t b, uint32_t
 // Every wait is bounded: on timeout the CTA raises the status word, waits
 // (bounded) for its own copies in flight and leaves.
 template <int NT, int NS>
-__global__ void __launch_bounds__(NT) classify_tma_kernel(const uint8_t* __restrict__ rec, uint64_t n,
+__global__ void __launch_bounds__(NT) classify_tma_kernel(const uint8_t* __restrict__ rec, KeyMask km, uint64_t n,
                                                           const uint64_t* __restrict__ t,
                                                           const uint32_t* __restrict__ lut, Pair* __restrict__ pairs,
                                                           uint32_t* __restrict__ hist, uint32_t* ctrl, uint32_t cshift,
-                                                          uint32_t* __restrict__ seg_hist, uint32_t seg_stride) {
+                                                          uint32_t* __restrict__ seg_hist, uint32_t seg_stride,
+                                                          long long wait_limit) {
   constexpr int KPT = NS * kTileRecs / NT;
   extern __shared__ __align__(128) uint8_t buf[];  // NS x kTileBytes
   __shared__ uint64_t bar[NS];
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(NT) classify_tma_kernel(const uint8_t* __restr
       const int slot = threadIdx.x + j * NT, s = slot / kTileRecs, r = slot % kTileRecs;
       w[j][0] = w[j][1] = w[j][2] = 0x20202020u;  // a key of spaces where the round has no tile
       if (k0 + s * G < ntiles) {
-        ok = ok && mbar_wait(&bar[s], round & 1, kWaitLimitCycles);
+        ok = ok && mbar_wait(&bar[s], round & 1, wait_limit);
         const uint32_t* ws = reinterpret_cast<const uint32_t*>(buf + s * kTileBytes + r * kRecord);
         w[j][0] = ws[0];
         w[j][1] = ws[1];
@@ -112,7 +113,7 @@ __global__ void __launch_bounds__(NT) classify_tma_kernel(const uint8_t* __restr
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
       const int slot = threadIdx.x + j * NT, s = slot / kTileRecs;
-      pr[j] = pair_from_words(w[j][0], w[j][1], w[j][2]);
+      pr[j] = pair_from_words(w[j][0], w[j][1], w[j][2], km);
       x[j] = enc9_pair(pr[j]);
       lo[j] = hi[j] = 0;
       if (k0 + s * G < ntiles) lut_range(lut, x[j], lo[j], hi[j]);
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(NT) classify_tma_kernel(const uint8_t* __restr
   // ragged tail (n mod 256 records, so CTA 0 alone): plain loads
   for (uint64_t i = ntiles * kTileRecs + blockIdx.x * (uint64_t)NT + threadIdx.x; i < n && blockIdx.x == 0;
        i += (uint64_t)NT) {
-    const uint32_t q = classify_one(load_pair(rec + i * kRecord, 0), i, t, lut, pairs, hist);
+    const uint32_t q = classify_one(load_pair(rec + i * kRecord, 0, km), i, t, lut, pairs, hist);
     if (seg_hist) atomicAdd(&hc[q >> cshift], 1u);
   }
   if (seg_hist) {
@@ -178,7 +179,7 @@ constexpr int kClassifyStages = ELSAR_CLASSIFY_NS;
 #define CLASSIFY_TMA classify_tma_kernel<kClassifyThreads, kClassifyStages>
 
 // Pass A, plain form (record buffers that are not 16-byte aligned).
-__global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __restrict__ rec, uint64_t n,
+__global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __restrict__ rec, KeyMask km, uint64_t n,
                                                             const uint64_t* __restrict__ t,
                                                             const uint32_t* __restrict__ lut,
                                                             Pair* __restrict__ pairs, uint32_t* __restrict__ hist,
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __res
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
       const uint64_t i = i0 + (uint64_t)u * kThreads;
-      if (i < n) p[u] = load_pair(rec + i * kRecord, 0);
+      if (i < n) p[u] = load_pair(rec + i * kRecord, 0, km);
     }
 #pragma unroll
     for (int u = 0; u < kUnroll; ++u) {
@@ -519,7 +520,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
                                                                        uint32_t seg_stride, uint32_t cshift,
                                                                        uint32_t C, Pair* __restrict__ out,
                                                                        uint32_t* ctrl, const uint64_t* __restrict__ poff,
-                                                                       uint32_t K) {
+                                                                       uint32_t K, long long wait_limit) {
   extern __shared__ __align__(128) uint8_t smem[];
   if (ctrl[kStatusWord]) return;
   const Stage S = carve_stage(smem, C);
@@ -578,7 +579,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
       }
   for (uint64_t j = 0; j < nbatch; ++j) {
     const int buf = (int)(j & 1);
-    const bool ok = mbar_wait(&S.bar[buf], (uint32_t)((j >> 1) & 1), kWaitLimitCycles);
+    const bool ok = mbar_wait(&S.bar[buf], (uint32_t)((j >> 1) & 1), wait_limit);
     Pair p[kStagePer];
     uint32_t bin[kStagePer];
 #pragma unroll
@@ -619,7 +620,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
 __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pair* __restrict__ in,
                                                                      const uint32_t* __restrict__ bin_off, uint32_t B,
                                                                      uint32_t cshift, Pair* __restrict__ out,
-                                                                     uint32_t* ctrl) {
+                                                                     uint32_t* ctrl, long long wait_limit) {
   extern __shared__ __align__(128) uint8_t smem[];
   if (ctrl[kStatusWord]) return;
   const uint32_t nf = 1u << cshift;
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pa
       }
   for (uint32_t j = 0; j < nbatch; ++j) {
     const int buf = (int)(j & 1);
-    const bool ok = mbar_wait(&S.bar[buf], (j >> 1) & 1, kWaitLimitCycles);
+    const bool ok = mbar_wait(&S.bar[buf], (j >> 1) & 1, wait_limit);
     const uint32_t i0 = s + j * kStagePairs;
     Pair p[kStagePer];
     uint32_t bin[kStagePer];
@@ -689,7 +690,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pa
 // Pass A over K record sets: record i of set k goes to global pair slot
 // poff[k] + i with the set's fine bin tbase[k] + q (binary search over the
 // set's own splitters).
-__global__ void __launch_bounds__(kThreads) classify_batch_kernel(const uint8_t* const* __restrict__ ins,
+__global__ void __launch_bounds__(kThreads) classify_batch_kernel(const uint8_t* const* __restrict__ ins, KeyMask km,
                                                                   const uint64_t* __restrict__ poff, uint32_t K,
                                                                   const uint64_t* __restrict__ t,
                                                                   const uint64_t* __restrict__ tbase,
@@ -704,7 +705,7 @@ __global__ void __launch_bounds__(kThreads) classify_batch_kernel(const uint8_t*
   for (uint64_t g = blockIdx.x * (uint64_t)kThreads + threadIdx.x; g < N; g += (uint64_t)gridDim.x * kThreads) {
     const uint32_t k = upper_set(poff, K, g);
     const uint64_t i = g - poff[k];
-    Pair p = load_pair(ins[k] + i * kRecord, 0);
+    Pair p = load_pair(ins[k] + i * kRecord, 0, km);
     const uint64_t x = enc9_pair(p);
     const uint64_t* tk = t + tbase[k];
     uint32_t lo = 0, hi = (1u << log2B[k]) - 1;
@@ -779,7 +780,7 @@ cudaError_t partition_batch(const BatchPartArgs& a) {
   const uint64_t segs = coarse_segments(a.N);
   const unsigned G = (unsigned)umin64(segs, (uint64_t)sms * 8);
   if (cshift > kStagedMaxShift) {  // bins too many for whole runs: one atomic pass
-    classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.poff, a.K, a.splitters, a.tbase, a.log2B,
+    classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.km, a.poff, a.K, a.splitters, a.tbase, a.log2B,
                                                  a.pairs_in_order, a.cursor, 0, nullptr, 0);
     scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
     scatter_atomic_kernel<<<G, kThreads, 0, st>>>(a.pairs_in_order, a.N, a.poff, a.K, a.cursor, a.pairs, a.ctrl);
@@ -791,15 +792,16 @@ cudaError_t partition_batch(const BatchPartArgs& a) {
   }
   // roles: input-order pairs and the final bin order share `pairs`; the
   // coarse order between the two passes lives in `pairs_in_order`
-  classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.poff, a.K, a.splitters, a.tbase, a.log2B, a.pairs, a.cursor,
-                                               cshift, a.seg_hist, (uint32_t)segs);
+  classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.km, a.poff, a.K, a.splitters, a.tbase, a.log2B, a.pairs,
+                                               a.cursor, cshift, a.seg_hist, (uint32_t)segs);
   scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
   coarse_offsets_kernel<<<(C + 7) / 8, 256, 0, st>>>(a.seg_hist, (uint32_t)segs, G, C, cshift, a.bin_off, a.ctrl);
   coarse_scatter_kernel<<<G, kStageThreads, stage_smem_bytes(C), st>>>(a.pairs, a.N, kThreads, 0, a.seg_hist,
                                                                         (uint32_t)segs, cshift, C, a.pairs_in_order,
-                                                                        a.ctrl, a.poff, a.K);
+                                                                        a.ctrl, a.poff, a.K, kWaitLimitCycles);
   fine_scatter_kernel<<<C, kStageThreads, stage_smem_bytes(1u << cshift), st>>>(a.pairs_in_order, a.bin_off, a.B,
-                                                                                 cshift, a.pairs, a.ctrl);
+                                                                                 cshift, a.pairs, a.ctrl,
+                                                                                 kWaitLimitCycles);
   mark_set_starts<<<(a.K + 255) / 256, 256, 0, st>>>(a.tbase, a.K, a.item_flag);
   items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize, a.ctrl);
   *a.launches += 7;
@@ -828,8 +830,8 @@ cudaError_t partition_records(const PartArgs& a) {
     G = (unsigned)umin64(segs, umax64(1, umin64(tiles, (uint64_t)sms * (occ > 0 ? occ : 1))));
     U = kTileRecs;
     tail_to_first = 1;
-    CLASSIFY_TMA<<<G, kClassifyThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl, cshift,
-                                                    a.seg_hist, (uint32_t)segs);
+    CLASSIFY_TMA<<<G, kClassifyThreads, smem, st>>>(a.records, a.km, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl, cshift,
+                                                    a.seg_hist, (uint32_t)segs, a.wait_limit);
   } else {
     const uint64_t per_block = (uint64_t)kThreads * kUnroll;
     const uint64_t blocks = (a.n + per_block - 1) / per_block;
@@ -838,8 +840,8 @@ cudaError_t partition_records(const PartArgs& a) {
     G = (unsigned)umin64(segs, umax64(1, umin64(blocks, (uint64_t)sms * (occ > 0 ? occ : 1))));
     U = (uint32_t)per_block;
     tail_to_first = 0;
-    classify_kernel<<<G, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, cshift, a.seg_hist,
-                                            (uint32_t)segs);
+    classify_kernel<<<G, kThreads, 0, st>>>(a.records, a.km, a.n, a.splitters, a.lut, pin, a.cursor, cshift,
+                                            a.seg_hist, (uint32_t)segs);
   }
   if (a.ev[0]) cudaEventRecord(a.ev[0], st);
   scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, B, a.bin_off, a.cursor, a.ctrl);
@@ -861,9 +863,10 @@ cudaError_t partition_records(const PartArgs& a) {
   cudaStreamIsCapturing(st, &cs);
   if (cs == cudaStreamCaptureStatusNone) prepare_scatter_kernels();
   coarse_scatter_kernel<<<G, kStageThreads, smem1, st>>>(pin, a.n, U, tail_to_first, a.seg_hist, seg_stride, cshift,
-                                                          C, static_cast<Pair*>(a.mid), a.ctrl, nullptr, 0);
+                                                          C, static_cast<Pair*>(a.mid), a.ctrl, nullptr, 0,
+                                                          a.wait_limit);
   fine_scatter_kernel<<<C, kStageThreads, smem2, st>>>(static_cast<const Pair*>(a.mid), a.bin_off, B, cshift,
-                                                        static_cast<Pair*>(a.pairs), a.ctrl);
+                                                        static_cast<Pair*>(a.pairs), a.ctrl, a.wait_limit);
   if (a.ev[2]) cudaEventRecord(a.ev[2], st);
   *a.launches += 6;
   return cudaGetLastError();
@@ -880,12 +883,12 @@ cudaError_t classify_accumulate(const PartArgs& a) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, CLASSIFY_TMA, kClassifyThreads, smem);
     const uint64_t tiles = a.n / kTileRecs;
     const unsigned grid = (unsigned)umax64(1, umin64(tiles, (uint64_t)sms * (occ > 0 ? occ : 1)));
-    CLASSIFY_TMA<<<grid, kClassifyThreads, smem, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl, 0,
-                                                       nullptr, 0);
+    CLASSIFY_TMA<<<grid, kClassifyThreads, smem, st>>>(a.records, a.km, a.n, a.splitters, a.lut, pin, a.cursor, a.ctrl, 0,
+                                                       nullptr, 0, a.wait_limit);
   } else {
     const uint64_t per_block = (uint64_t)kThreads * kUnroll;
     const unsigned grid = (unsigned)umax64(1, umin64((a.n + per_block - 1) / per_block, (uint64_t)sms * 4));
-    classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.n, a.splitters, a.lut, pin, a.cursor, 0, nullptr, 0);
+    classify_kernel<<<grid, kThreads, 0, st>>>(a.records, a.km, a.n, a.splitters, a.lut, pin, a.cursor, 0, nullptr, 0);
   }
   *a.launches += 1;
   return cudaGetLastError();

@@ -14,16 +14,69 @@
 // Schedules: PERSISTENT = one launch, CTAs pull items from a global queue
 // (oversize items first) -- the GPU form of the paper's dynamic scheduling of
 // uneven partitions; PER_PARTITION = one launch per partition.
+//
+// Each CTA is warp-specialised: 8 sorter warps sort the next items in shared
+// memory while kGatherWarps gatherer warps move the records of earlier ones,
+// so that the sort's shared-memory work overlaps the gather's DRAM traffic.
+// The sorters hand each sorted item over as a list of record indices in a
+// ring of kSlots shared-memory slots (item s in slot s mod kSlots); named
+// barriers FULL[b] (sorters arrive, gatherers wait) and EMPTY[b] (gatherers
+// arrive, sorters wait before refilling slot b) order the two groups, every
+// phase of each barrier taking exactly the 256 sorter and the gatherer
+// threads once.
 #include "common.cuh"
 
 namespace elsar {
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 256;  // sorter threads (warps 0-7)
 constexpr int kWarps = kThreads / 32;
+#ifndef ELSAR_GATHER_WARPS
+#define ELSAR_GATHER_WARPS 6
+#endif
+constexpr int kGatherWarps = ELSAR_GATHER_WARPS;  // gatherer warps (after the sorters)
+constexpr int kBlockThreads = kThreads + 32 * kGatherWarps;
+constexpr uint32_t kSlots = 3;      // hand-over ring between the sorters and the gatherers
 constexpr uint32_t kRankMax = 128;  // buckets up to this length are ranked inside the digit pass (the touch-up)
 
+// named barriers: 1 = the sorter group; FULL[b] = 2 + b and EMPTY[b] = 2 + kSlots + b over the
+// whole CTA (immediate ids, so that the kernel reserves only the barriers it uses)
+__device__ __forceinline__ void sorter_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
+#define ELSAR_BAR(op, id) asm volatile("bar." op " " #id ", %0;" ::"n"(kBlockThreads) : "memory")
+__device__ __forceinline__ void full_arrive(uint32_t b) {
+  if (b == 0) ELSAR_BAR("arrive", 2);
+  else if (b == 1) ELSAR_BAR("arrive", 3);
+  else ELSAR_BAR("arrive", 4);
+}
+__device__ __forceinline__ void full_wait(uint32_t b) {
+  if (b == 0) ELSAR_BAR("sync", 2);
+  else if (b == 1) ELSAR_BAR("sync", 3);
+  else ELSAR_BAR("sync", 4);
+}
+__device__ __forceinline__ void empty_arrive(uint32_t b) {
+  if (b == 0) ELSAR_BAR("arrive", 5);
+  else if (b == 1) ELSAR_BAR("arrive", 6);
+  else ELSAR_BAR("arrive", 7);
+}
+__device__ __forceinline__ void empty_wait(uint32_t b) {
+  if (b == 0) ELSAR_BAR("sync", 5);
+  else if (b == 1) ELSAR_BAR("sync", 6);
+  else ELSAR_BAR("sync", 7);
+}
+static_assert(kSlots == 3, "the barrier helpers above name three slots");
+
+// A sorted item handed from the sorters to the gatherers.
+struct Handoff {
+  uint64_t o0;            // first output record of the item (inside its record set)
+  const uint8_t* in;      // the set's input records
+  uint8_t* out;           // the set's output records
+  const Pair* gsorted;    // mode 1: the item's sorted pairs in global memory
+  uint32_t m;             // records
+  uint32_t mode;          // 0: record indices in the slot's index list, 1: gsorted, 2: no more items
+};
+
 struct Misc {
+  Handoff ho[kSlots];
   uint64_t red[2][kWarps];
   uint64_t kmin, kmax;
   uint32_t nlong, next_long;
@@ -41,7 +94,9 @@ struct Tile {
   uint16_t* perm2; // cap: scatter target
   uint32_t* longs; // cap/kRankMax + 1 long runs of the first digit pass
   uint32_t* stk;   // kWarps x (cap/kRankMax + 1) refinement stacks
-  uint32_t stk_cap;
+  uint32_t* idx;   // kSlots x cap: record indices of the items handed to the gatherers
+  uint64_t* enc;   // cap: base-95 encodings of the tile's keys (computed once per item)
+  uint32_t stk_cap, cap;
   Misc* ms;
 };
 
@@ -65,12 +120,11 @@ struct KArgs {
 };
 
 // key used by a digit pass: 0 = base-95 encoding (dense for printable keys;
-// recomputed from the pair, which costs less than the shared memory a cache
-// of it would take from L1), 1 = raw key bytes 0-7, 2 = key bytes 8-9 and
-// index.  Encoding order agrees with byte order; equal encodings are split by
-// the raw bytes, then by lo.
+// cached in shared memory when the tile is loaded), 1 = raw key bytes 0-7,
+// 2 = key bytes 8-9 and index.  Encoding order agrees with byte order; equal
+// encodings are split by the raw bytes, then by lo.
 __device__ __forceinline__ uint64_t sel_key(const Tile& t, uint32_t j, int sel) {
-  return sel == 0 ? enc9_pair(t.A[j]) : (sel == 1 ? t.A[j].hi : t.A[j].lo);
+  return sel == 0 ? t.enc[j] : (sel == 1 ? t.A[j].hi : t.A[j].lo);
 }
 
 __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* wsum) {
@@ -81,7 +135,7 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* wsum) 
     if (lane >= (uint32_t)d) incl += y;
   }
   if (lane == 31) wsum[warp] = incl;
-  __syncthreads();
+  sorter_sync();
   if (warp == 0) {
     uint32_t w = lane < (uint32_t)kWarps ? wsum[lane] : 0;
     uint32_t wi = w;
@@ -91,9 +145,9 @@ __device__ __forceinline__ uint32_t block_scan_excl(uint32_t v, uint32_t* wsum) 
     }
     if (lane < (uint32_t)kWarps) wsum[lane] = wi - w;
   }
-  __syncthreads();
+  sorter_sync();
   uint32_t r = wsum[warp] + incl - v;
-  __syncthreads();
+  sorter_sync();
   return r;
 }
 
@@ -114,7 +168,7 @@ __device__ void block_minmax(const Tile& t, uint32_t m, int sel) {
     t.ms->red[0][warp] = mn;
     t.ms->red[1][warp] = mx;
   }
-  __syncthreads();
+  sorter_sync();
   if (threadIdx.x == 0) {
     uint64_t a = ~0ull, b = 0;
     for (int w = 0; w < kWarps; ++w) {
@@ -124,7 +178,7 @@ __device__ void block_minmax(const Tile& t, uint32_t m, int sel) {
     t.ms->kmin = a;
     t.ms->kmax = b;
   }
-  __syncthreads();
+  sorter_sync();
 }
 
 // After a digit pass: position pos of perm holds record j of the bucket
@@ -259,7 +313,7 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
   Misc& ms = *t.ms;
   if (m <= 1) {
     if (threadIdx.x == 0 && m == 1) t.perm[0] = 0;
-    __syncthreads();
+    sorter_sync();
     return;
   }
   int sel = 0;
@@ -283,10 +337,10 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
     ms.nlong = 0;
     ms.next_long = 0;
   }
-  __syncthreads();
+  sorter_sync();
   for (uint32_t j = threadIdx.x; j < m; j += kThreads)
     atomicAdd(t.cnt + (uint32_t)((sel_key(t, j, sel) - kmin) >> shift), 1u);
-  __syncthreads();
+  sorter_sync();
   {
     const uint32_t per = (D + kThreads - 1) / kThreads;
     const uint32_t b = min(D, threadIdx.x * per), e = min(D, b + per);
@@ -299,25 +353,25 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
       run += c;
     }
   }
-  __syncthreads();
+  sorter_sync();
   for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
     const uint32_t pos = atomicAdd(t.cnt + (uint32_t)((sel_key(t, j, sel) - kmin) >> shift), 1u);
     t.perm[pos] = (uint16_t)j;
   }
-  __syncthreads();
+  sorter_sync();
   // buckets up to kRankMax ranked in place (every element by its own thread)
   for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
     const uint32_t d = (uint32_t)((sel_key(t, t.perm[pos], sel) - kmin) >> shift);
     place_ranked(t, pos, d ? t.cnt[d - 1] : 0, t.cnt[d]);
   }
-  __syncthreads();
+  sorter_sync();
   for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) t.perm[pos] = t.perm2[pos];
   for (uint32_t d = threadIdx.x; d < D; d += kThreads) {
     const uint32_t s = d ? t.cnt[d - 1] : 0, e = t.cnt[d];
     const uint32_t len = e - s;
     if (len > kRankMax) t.longs[atomicAdd(&ms.nlong, 1u)] = (s << 16) | len;
   }
-  __syncthreads();
+  sorter_sync();
   const uint32_t lane = threadIdx.x & 31;
   for (;;) {
     uint32_t r = 0;
@@ -327,25 +381,27 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
     const uint32_t ent = t.longs[r];
     warp_refine(t, ent >> 16, ent & 0xFFFFu);
   }
-  __syncthreads();
+  sorter_sync();
 }
 
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
-// Gather m records in sorted order into out[o0, o0 + m): warp-cooperative,
-// 32 records (800 words) per step, loads and stores both coalesced.  While a
-// warp loads one group it asks L2 for the lines of its next group, so twice as
-// many records are in flight without holding more registers.
+// Gather m records in sorted order into out[o0, o0 + m) by the gatherer
+// warps: warp-cooperative, 32 records (800 words) per step, loads and stores
+// both coalesced.  While a warp loads one group it asks L2 for the lines of
+// its next group, so twice as many records are in flight without holding
+// more registers.
 template <typename IdxFn>
 __device__ __forceinline__ void gather(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, uint64_t o0,
                                        uint32_t m, IdxFn idx_of) {
-  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr uint32_t kStride = 32 * kGatherWarps;
+  const uint32_t lane = threadIdx.x & 31, warp = (threadIdx.x - kThreads) >> 5;
   const uint32_t* __restrict__ in32 = reinterpret_cast<const uint32_t*>(in);
   uint32_t* __restrict__ out32 = reinterpret_cast<uint32_t*>(out);
-  for (uint32_t j0 = warp * 32; j0 < m; j0 += kThreads) {
+  for (uint32_t j0 = warp * 32; j0 < m; j0 += kStride) {
     const uint32_t nrec = min(32u, m - j0);
     const uint32_t my = lane < nrec ? idx_of(j0 + lane) : 0;
-    const uint32_t jn = j0 + kThreads + lane;
+    const uint32_t jn = j0 + kStride + lane;
     if (jn < m) {
       const uint8_t* r = in + (uint64_t)idx_of(jn) * kRecord;
       prefetch_l2(r);
@@ -381,8 +437,12 @@ __device__ __forceinline__ uint32_t merge_split(const Pair* a, uint32_t na, cons
 }
 
 __device__ __forceinline__ void load_tile(const Tile& t, const Pair* src, uint32_t m) {
-  for (uint32_t j = threadIdx.x; j < m; j += kThreads) t.A[j] = src[j];
-  __syncthreads();
+  for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
+    const Pair p = src[j];
+    t.A[j] = p;
+    t.enc[j] = enc9_pair(p);
+  }
+  sorter_sync();
 }
 
 // items above cap: sort cap-sized chunks in place, then merge passes between
@@ -397,7 +457,7 @@ __device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0,
     load_tile(t, src + o0 + c0, mc);
     tile_sort(t, mc);
     for (uint32_t j = threadIdx.x; j < mc; j += kThreads) src[o0 + c0 + j] = t.A[t.perm[j]];
-    __syncthreads();
+    sorter_sync();
   }
   Pair* A = t.A;
   for (uint32_t w = cap; w < m; w *= 2) {
@@ -408,13 +468,13 @@ __device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0,
       const Pair* ga = src + o0 + p0;
       const Pair* gb = src + o0 + a1;
       if (threadIdx.x < 2) ms.split[threadIdx.x] = merge_split(ga, a1 - p0, gb, b1 - a1, (threadIdx.x ? t1 : t0) - p0);
-      __syncthreads();
+      sorter_sync();
       const uint32_t ka0 = (uint32_t)ms.split[0], ka1 = (uint32_t)ms.split[1];
       const uint32_t kb0 = (t0 - p0) - ka0, kb1 = (t1 - p0) - ka1;
       const uint32_t na = ka1 - ka0, nb = kb1 - kb0;
       for (uint32_t j = threadIdx.x; j < na; j += kThreads) A[j] = ga[ka0 + j];
       for (uint32_t j = threadIdx.x; j < nb; j += kThreads) A[na + j] = gb[kb0 + j];
-      __syncthreads();
+      sorter_sync();
       const uint32_t tot = na + nb;
       const uint32_t per = (tot + kThreads - 1) / kThreads;
       const uint32_t d = threadIdx.x * per;
@@ -431,12 +491,12 @@ __device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0,
           dst[o0 + t0 + d + q] = takeA ? A[ia++] : A[na + ib++];
         }
       }
-      __syncthreads();
+      sorter_sync();
     }
     Pair* tmp = src;
     src = dst;
     dst = tmp;
-    __syncthreads();
+    sorter_sync();
   }
   return src;
 }
@@ -451,10 +511,12 @@ __device__ __forceinline__ uint32_t set_of_bin(const uint64_t* __restrict__ tbas
   return lo;
 }
 
-__device__ void process_item(const KArgs& k, const Tile& t, uint32_t it, uint32_t num_items) {
+// Sorter side of one work item: sort it and hand it to the gatherers in slot
+// (slot mod kSlots).  Returns false for an empty item (nothing handed over).
+__device__ bool sort_item(const KArgs& k, const Tile& t, uint32_t it, uint32_t num_items, uint32_t slot) {
   const uint64_t o0 = k.bin_off[k.items[it]];
   const uint32_t m = k.bin_off[k.items[it + 1]] - (uint32_t)o0;
-  if (m == 0) return;
+  if (m == 0) return false;
   // records of this item: one set's buffers (batched path) or the only set
   const uint8_t* in = k.in;
   uint8_t* out = k.out;
@@ -471,15 +533,60 @@ __device__ void process_item(const KArgs& k, const Tile& t, uint32_t it, uint32_
     const uint64_t a = k.bin_off[k.items[nx]], b = k.bin_off[k.items[nx + 1]];
     for (uint64_t q = a * sizeof(Pair); q < b * sizeof(Pair); q += 128) prefetch_l2(reinterpret_cast<const uint8_t*>(k.pairs) + q);
   }
+  const uint32_t b = slot % kSlots;
+  Handoff h;
+  h.o0 = o0 - base;
+  h.in = in;
+  h.out = out;
+  h.m = m;
   if (m <= k.cap) {
     load_tile(t, k.pairs + o0, m);
     tile_sort(t, m);
-    gather(in, out, o0 - base, m, [&](uint32_t j) { return (uint32_t)t.A[t.perm[j]].lo; });
+    if (slot >= kSlots) empty_wait(b);  // the gatherers are done with this slot's previous item
+    uint32_t* idx = t.idx + b * t.cap;
+    for (uint32_t j = threadIdx.x; j < m; j += kThreads) idx[j] = (uint32_t)t.A[t.perm[j]].lo;
+    h.gsorted = nullptr;
+    h.mode = 0;
   } else {
     const Pair* sorted = sort_oversize(k, t, o0, m);
-    gather(in, out, o0 - base, m, [&](uint32_t j) { return (uint32_t)sorted[o0 + j].lo; });
+    if (slot >= kSlots) empty_wait(b);
+    h.gsorted = sorted + o0;
+    h.mode = 1;
   }
-  __syncthreads();
+  if (threadIdx.x == 0) t.ms->ho[b] = h;
+  __threadfence_block();  // global (oversize) and shared writes before the hand-over
+  full_arrive(b);
+  return true;
+}
+
+// Sorter side: no more items.  Slot n (the number handed over) says so; then
+// the gatherers' releases of the last items still unclaimed are taken, so
+// that every phase of every EMPTY barrier has completed when the sorters leave.
+__device__ void sorters_done(const Tile& t, uint32_t n) {
+  const uint32_t b = n % kSlots;
+  if (n >= kSlots) empty_wait(b);  // releases item n - kSlots
+  if (threadIdx.x == 0) t.ms->ho[b].mode = 2;
+  __threadfence_block();
+  full_arrive(b);
+  for (uint32_t s = n >= kSlots ? n - kSlots + 1 : 0; s < n; ++s) empty_wait(s % kSlots);
+}
+
+// Gatherer side: items in slot order until the sorters say there are no more.
+__device__ void gatherer_loop(const Tile& t) {
+  for (uint32_t slot = 0;; ++slot) {
+    const uint32_t b = slot % kSlots;
+    full_wait(b);
+    const Handoff h = t.ms->ho[b];
+    if (h.mode == 2) break;
+    if (h.mode == 0) {
+      const uint32_t* idx = t.idx + b * t.cap;
+      gather(h.in, h.out, h.o0, h.m, [&](uint32_t j) { return idx[j]; });
+    } else {
+      const Pair* g = h.gsorted;
+      gather(h.in, h.out, h.o0, h.m, [&](uint32_t j) { return (uint32_t)g[j].lo; });
+    }
+    empty_arrive(b);
+  }
 }
 
 __device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
@@ -498,24 +605,35 @@ __device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
   p += (size_t)t.stk_cap * 4;
   t.stk = reinterpret_cast<uint32_t*>(p);
   p += (size_t)kWarps * t.stk_cap * 4;
+  t.idx = reinterpret_cast<uint32_t*>(p);
+  p += (size_t)kSlots * cap * 4;
+  p = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
+  t.enc = reinterpret_cast<uint64_t*>(p);
+  p += (size_t)cap * 8;
+  t.cap = cap;
   p = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
   t.ms = reinterpret_cast<Misc*>(p);
   return t;
 }
 
-__global__ void __launch_bounds__(kThreads, 3) sort_gather_kernel(KArgs k) {
+__global__ void __launch_bounds__(kBlockThreads, 2) sort_gather_kernel(KArgs k) {
   extern __shared__ __align__(16) uint8_t smem[];
-  if (k.ctrl[kStatusWord]) return;  // partitioning gave up: no item is valid
+  if (k.ctrl[kStatusWord]) return;  // partitioning gave up: no item is valid (uniform over the CTA)
   const Tile t = carve(smem, k.cap);
+  if (threadIdx.x >= kThreads) {
+    gatherer_loop(t);
+    return;
+  }
   Misc& ms = *t.ms;
   const uint32_t num_items = k.ctrl[kNumItems];
+  uint32_t slot = 0;
   if (k.persistent) {
     const uint32_t num_over = k.ctrl[kNumOversize];
     for (;;) {
       if (threadIdx.x == 0) ms.item = atomicAdd(k.ctrl + kQueueHead, 1u);
-      __syncthreads();
+      sorter_sync();
       const uint32_t j = ms.item;
-      __syncthreads();
+      sorter_sync();
       if (j >= num_over + num_items) break;
       uint32_t it;
       if (j < num_over) {
@@ -524,12 +642,14 @@ __global__ void __launch_bounds__(kThreads, 3) sort_gather_kernel(KArgs k) {
         it = j - num_over;
         if (k.bin_off[k.items[it + 1]] - k.bin_off[k.items[it]] > k.cap) continue;  // done in the oversize phase
       }
-      process_item(k, t, it, num_items);
+      if (sort_item(k, t, it, num_items, slot)) ++slot;
     }
   } else {
     const uint32_t i0 = k.part_items[k.part], i1 = k.part_items[k.part + 1];
-    for (uint32_t it = i0 + blockIdx.x; it < i1; it += gridDim.x) process_item(k, t, it, 0);
+    for (uint32_t it = i0 + blockIdx.x; it < i1; it += gridDim.x)
+      if (sort_item(k, t, it, 0, slot)) ++slot;
   }
+  sorters_done(t, slot);
 }
 
 // item range of each partition (per-partition schedule): item id of the partition's first bin
@@ -544,7 +664,7 @@ __global__ void part_items_kernel(const uint32_t* cuts, const uint32_t* item_of_
 
 size_t sort_smem_bytes(uint32_t cap) {
   const size_t stk = (size_t)(cap / kRankMax + 1) * 4;
-  return (size_t)cap * (sizeof(Pair) + 4 + 2 + 2) + stk * (1 + kWarps) + 16 + sizeof(Misc);
+  return (size_t)cap * (sizeof(Pair) + 4 + 2 + 2 + kSlots * 4 + 8) + stk * (1 + kWarps) + 32 + sizeof(Misc);
 }
 
 cudaError_t prepare_sort_kernel(uint32_t cap) {
@@ -576,12 +696,12 @@ cudaError_t sort_items(const SortArgs& a) {
     if (err != cudaSuccess) return err;
   }
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_gather_kernel, kThreads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sort_gather_kernel, kBlockThreads, smem);
   if (per_sm < 1) per_sm = 1;
   const int sms = sm_count();
   if (a.schedule == 1) {
     k.persistent = 1;
-    sort_gather_kernel<<<sms * per_sm, kThreads, smem, a.stream>>>(k);
+    sort_gather_kernel<<<sms * per_sm, kBlockThreads, smem, a.stream>>>(k);
     *a.launches += 1;
   } else {
     // one launch per partition; part_items computed on the device from the cuts
@@ -593,7 +713,7 @@ cudaError_t sort_items(const SortArgs& a) {
     const int grid = sms * per_sm < 64 ? sms * per_sm : 64;
     for (uint32_t p = 0; p < a.P; ++p) {
       k.part = p;
-      sort_gather_kernel<<<grid, kThreads, smem, a.stream>>>(k);
+      sort_gather_kernel<<<grid, kBlockThreads, smem, a.stream>>>(k);
     }
     *a.launches += 1 + a.P;
   }

@@ -37,7 +37,8 @@ FAKE_WS = 1 << 20  # never dereferenced: every case below is rejected before any
 
 @pytest.mark.parametrize("field,value", [("num_partitions", 1000), ("num_partitions", 1 << 17), ("tile_pairs", 300),
                                          ("tile_pairs", 1 << 14), ("sample_size", 1 << 24), ("balance", 2),
-                                         ("schedule", 5), ("model_kind", 9), ("fine_bins_log2", 23)])
+                                         ("schedule", 5), ("model_kind", 9), ("fine_bins_log2", 23),
+                                         ("skip_checks", 8), ("key_bytes", 11), ("wait_limit_cycles", 1 << 41)])
 def test_bad_params_rejected(field, value):
     p = elsar.Params(**{field: value})
     rc = elsar.lib().elsar_sort(FAKE_WS, FAKE_WS * 2, 1000, ctypes.byref(p.c()), FAKE_WS, 1 << 40, None, None)
@@ -88,3 +89,17 @@ def test_ooc_arguments_rejected_on_host():
     assert L.elsar_sort_ooc(FAKE_WS, FAKE_WS, 1000, ctypes.byref(p), FAKE_WS + 8, 1 << 40, None, None) == 1
     assert L.elsar_sort_ooc(None, None, 0, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 0
     assert elsar.ooc_min_workspace(10**9) > elsar.ooc_min_workspace(10**3) > 64 << 20
+
+
+def test_mlp_adam_arguments_rejected_on_host():
+    L = elsar.lib()
+    assert L.elsar_mlp_adam(FAKE_WS, FAKE_WS, FAKE_WS, FAKE_WS, 0, 1e-3, None) == 1  # t starts at 1
+    assert L.elsar_mlp_adam(None, FAKE_WS, FAKE_WS, FAKE_WS, 1, 1e-3, None) == 1
+
+
+def test_params_struct_matches_header():
+    """The binding's parameter and stats structs have the sizes the header's
+    field lists give (8 u32 + 2 u64 + 2 u32 + 1 u64; 8 floats + 4 u32 + 2 u64 +
+    6 u32 + 2 floats)."""
+    assert ctypes.sizeof(elsar._Params) == 8 * 4 + 2 * 8 + 2 * 4 + 8
+    assert ctypes.sizeof(elsar._Stats) == 8 * 4 + 4 * 4 + 2 * 8 + 6 * 4 + 2 * 4

@@ -32,3 +32,37 @@ def test_bounded_wait_times_out_and_context_survives():
     elsar.sort(d_in, d_out, n, elsar.Params(num_partitions=64))
     torch.cuda.synchronize()
     assert np.array_equal(d_out.cpu().numpy(), oracle.stable_sort(host))
+
+
+@pytest.mark.parametrize("in_off", [0, 4])
+def test_production_waits_run_out_and_the_next_sort_is_exact(in_off):
+    """The bounded waits of the sort's own bulk-copy pipelines, made to run
+    out by a wait limit of one clock cycle (each CTA's first wait starts right
+    after its copy is issued, long before the copy lands).  16-byte-aligned
+    records: classify's tile waits give up; 4-byte-aligned records take the
+    plain-load classify, and the coarse scatter's batch waits give up.  The
+    CTA raises the status word, drains its own copies and returns; every later
+    kernel reads the word and does nothing, so the sort kernel writes no record;
+    the call returns ELSAR_ETIMEOUT, and the next call on the same workspace
+    sorts exactly."""
+    n = 200_000
+    host = recgen.generate_cpu(n, recgen.KeySpec("zipf", s=1.1, dup=0.05, seed=14))
+    big = torch.zeros(n * 100 + 16, dtype=torch.uint8, device="cuda")
+    d_in = big[in_off:in_off + n * 100]
+    d_in.copy_(torch.from_numpy(host).cuda())
+    d_out = torch.full((n * 100,), 0xEE, dtype=torch.uint8, device="cuda")
+    p = elsar.Params(num_partitions=64, seed=3, wait_limit_cycles=1)
+    ws = elsar.alloc_workspace(n, p)
+    with pytest.raises(elsar.ElsarError) as e:
+        elsar.sort(d_in, d_out, n, p, ws=ws)
+    assert e.value.status == 4  # ELSAR_ETIMEOUT
+    torch.cuda.synchronize()
+    out = d_out.cpu().numpy().reshape(n, 100)
+    if in_off == 0:
+        assert np.all(out == 0xEE)  # nothing downstream of classify ran
+    # whatever the scatter left between its passes, no sorted record was gathered
+    assert not np.array_equal(d_out.cpu().numpy(), oracle.stable_sort(host))
+    p.wait_limit_cycles = 0
+    elsar.sort(d_in, d_out, n, p, ws=ws)
+    torch.cuda.synchronize()
+    assert np.array_equal(d_out.cpu().numpy(), oracle.stable_sort(host))

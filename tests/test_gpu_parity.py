@@ -18,6 +18,7 @@ SPECS = {
     "uniform": recgen.KeySpec("uniform", seed=1),
     "zipf11": recgen.KeySpec("zipf", s=1.1, dup=0.05, seed=3),
     "zipf13": recgen.KeySpec("zipf", s=1.3, dup=0.10, seed=5),
+    "prefix": recgen.KeySpec("prefix", seed=8),  # the paper's table-of-prefixes skew (Sec. 7.1)
 }
 
 
@@ -125,7 +126,7 @@ def test_uniform_1M_64_partitions():
     assert oracle.validate(host, got) == 0
 
 
-@pytest.mark.parametrize("name", ["zipf11", "zipf13"])
+@pytest.mark.parametrize("name", ["zipf11", "zipf13", "prefix"])
 @pytest.mark.parametrize("balance,schedule", [(0, 0), (1, 1), (1, 0), (0, 1)])
 def test_skewed_sort_matches_oracle(name, balance, schedule):
     n, P, S, seed = 400_000, 256, 4000, 9
@@ -217,9 +218,10 @@ def test_unfitted_model_rejected():
     assert e.value.status == 6
 
 
-def test_generator_twins_agree():
+@pytest.mark.parametrize("name", ["zipf13", "prefix"])
+def test_generator_twins_agree(name):
     n = 1_000_000
-    spec = SPECS["zipf13"]
+    spec = SPECS[name]
     d = torch.empty(n * 100, dtype=torch.uint8, device="cuda")
     recgen.generate_gpu(d, n, spec)
     torch.cuda.synchronize()
@@ -291,3 +293,66 @@ def test_unaligned_record_buffers(n, in_off, out_off):
     assert np.array_equal(d_out.cpu().numpy(), oracle.stable_sort(host))
     # the bytes around the output are untouched
     assert int(big_out[:out_off].sum()) == 0 and int(big_out[out_off + n * 100:].sum()) == 0
+
+
+# ---------------------------------------------------------------- radix partitioning (the paper's comparison)
+@pytest.mark.parametrize("name", ["uniform", "zipf11"])
+@pytest.mark.parametrize("balance", [0, 1])
+def test_radix_partition_matches_oracle(name, balance):
+    """model_kind RADIX: equal-width slices of the key domain.  The fine bin of
+    every record, the bin counts and the partition offsets equal the oracle's
+    radix classification, and the sort output equals the oracle's."""
+    n, P = 300_000, 64
+    host = recgen.generate_cpu(n, SPECS[name])
+    p = elsar.Params(num_partitions=P, seed=3, balance=balance, model_kind=elsar.MODEL_RADIX)
+    d_rec, ws, model = _fit(host, p, n)
+    hdr, _, spl = elsar.read_model(model, p, n)
+    log2B = hdr["log2B"]
+    assert hdr["kind"] == elsar.MODEL_RADIX and np.array_equal(spl, oracle.radix_splitters(log2B))
+    B = 1 << log2B
+    pairs = torch.empty(n * 16, dtype=torch.uint8, device="cuda")
+    bin_off = torch.empty(B + 1, dtype=torch.int32, device="cuda")
+    part_off = torch.empty(P + 1, dtype=torch.int64, device="cuda")
+    elsar.partition(model, d_rec, n, p, pairs, bin_off, part_off, ws)
+    torch.cuda.synchronize()
+    want, det = oracle.sort_by_splitters(host, oracle.radix_splitters(log2B), log2B, P, balance)
+    assert np.array_equal(det["q"], oracle.radix_bins(oracle.encode9_records(host), log2B))
+    bo = bin_off.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert np.array_equal(np.diff(bo), det["bin_counts"].astype(np.int64))
+    assert np.array_equal(part_off.cpu().numpy().astype(np.uint64), det["part_off"])
+    got, st = _sort_gpu(host, n, p)
+    assert st["model_used"] == elsar.MODEL_RADIX
+    assert np.array_equal(got, want)
+
+
+def test_partition_size_variance_radix_vs_models():
+    """Sec. 3.3: model-based partitions vary less in size than radix-based
+    ones on skewed keys.  Partition sizes under the paper's cut rule on 2M
+    Zipf(1.1) records with 5 % duplicates, 256 partitions: the RMI's and the
+    network's (kept whatever its checks say) against equal-width slices; each
+    side's sizes equal the oracle's."""
+    n, P, S, seed = 2_000_000, 256, 20_000, 5
+    host = recgen.generate_cpu(n, SPECS["zipf11"])
+    d_in = torch.from_numpy(host).cuda()
+    sizes = {}
+    for kind, skip in ((elsar.MODEL_RADIX, 0), (elsar.MODEL_RMI, 0), (elsar.MODEL_MLP, 7)):
+        p = elsar.Params(num_partitions=P, sample_size=S, seed=seed, balance=elsar.BALANCE_PAPER, model_kind=kind,
+                         skip_checks=skip)
+        d_rec, ws, model = _fit(host, p, n)
+        hdr, _, spl = elsar.read_model(model, p, n)
+        B = 1 << hdr["log2B"]
+        pairs = torch.empty(n * 16, dtype=torch.uint8, device="cuda")
+        bin_off = torch.empty(B + 1, dtype=torch.int32, device="cuda")
+        part_off = torch.empty(P + 1, dtype=torch.int64, device="cuda")
+        elsar.partition(model, d_rec, n, p, pairs, bin_off, part_off, ws)
+        torch.cuda.synchronize()
+        off = part_off.cpu().numpy().astype(np.uint64)
+        _, det = oracle.sort_by_splitters(host, spl, hdr["log2B"], P, balance=0, want_out=False)
+        assert np.array_equal(off, det["part_off"])
+        sizes[kind] = np.diff(off.astype(np.int64))
+    cv = {k: v.std() / v.mean() for k, v in sizes.items()}
+    print("\npartition size std/mean (paper rule, 256 partitions, 2M Zipf 1.1 records):",
+          {"radix": round(cv[elsar.MODEL_RADIX], 4), "rmi": round(cv[elsar.MODEL_RMI], 4),
+           "network": round(cv[elsar.MODEL_MLP], 4)})
+    assert cv[elsar.MODEL_RMI] < 0.5 * cv[elsar.MODEL_RADIX]
+    assert cv[elsar.MODEL_MLP] < cv[elsar.MODEL_RADIX]

@@ -6,7 +6,8 @@ device-wide synchronisation of cudaFree) pass only their input and output
 records; the library works in its own built-in scratch array.  This checks,
 through the C ABI, that its output equals the ordinary workspace sort on two
 calls in a row (the second call reuses the scratch the first one left behind),
-and that a size beyond the scratch is refused.  The file name makes pytest
+that both equal the oracle's stable sort, and that a size beyond the scratch
+is refused.  The file name makes pytest
 collect it last.
 """
 import ctypes
@@ -15,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_2305_05671_b300 as elsar
 import recgen
 
@@ -36,6 +38,7 @@ def test_noalloc_equals_workspace_sort_twice():
         assert rc == 0, L.elsar_last_error()
         torch.cuda.synchronize()
         assert torch.equal(got, want)
+        assert np.array_equal(got.cpu().numpy(), oracle.stable_sort(d_in.cpu().numpy()))
     # more records than the built-in scratch holds: refused before any device work
     big = 2_000_000
     rc = L.elsar_sort_noalloc(d_in.data_ptr(), got.data_ptr(), big, ctypes.byref(p.c()), stream)
