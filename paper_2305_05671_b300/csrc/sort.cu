@@ -32,7 +32,7 @@ namespace {
 constexpr int kThreads = 256;  // sorter threads (warps 0-7)
 constexpr int kWarps = kThreads / 32;
 #ifndef ELSAR_GATHER_WARPS
-#define ELSAR_GATHER_WARPS 6
+#define ELSAR_GATHER_WARPS 4
 #endif
 constexpr int kGatherWarps = ELSAR_GATHER_WARPS;  // gatherer warps (after the sorters)
 constexpr int kBlockThreads = kThreads + 32 * kGatherWarps;
@@ -387,10 +387,11 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
 // Gather m records in sorted order into out[o0, o0 + m) by the gatherer
-// warps: warp-cooperative, 32 records (800 words) per step, loads and stores
-// both coalesced.  While a warp loads one group it asks L2 for the lines of
-// its next group, so twice as many records are in flight without holding
-// more registers.
+// warps, 32 records per warp step: lanes 0-24 each move word `lane` of every
+// record of the group (one broadcast shuffle, one load and one store per
+// word: a record's 25 words are one coalesced 100-byte access).  While a warp
+// moves one group it asks L2 for the lines of its next group, so twice as
+// many records are in flight without holding more registers.
 template <typename IdxFn>
 __device__ __forceinline__ void gather(const uint8_t* __restrict__ in, uint8_t* __restrict__ out, uint64_t o0,
                                        uint32_t m, IdxFn idx_of) {
@@ -407,20 +408,16 @@ __device__ __forceinline__ void gather(const uint8_t* __restrict__ in, uint8_t* 
       prefetch_l2(r);
       prefetch_l2(r + kRecord - 1);
     }
-    uint32_t v[25];
+    uint32_t v[32];
 #pragma unroll
-    for (int it = 0; it < 25; ++it) {
-      const uint32_t w = lane + 32u * it;
-      const uint32_t r = w / 25u, k = w - 25u * r;
+    for (int r = 0; r < 32; ++r) {
       const uint32_t src = __shfl_sync(0xffffffffu, my, r);
-      v[it] = r < nrec ? __ldg(in32 + (uint64_t)src * 25u + k) : 0u;
+      v[r] = (lane < 25u && (uint32_t)r < nrec) ? __ldg(in32 + (uint64_t)src * 25u + lane) : 0u;
     }
-    uint32_t* dst = out32 + (o0 + j0) * 25u;
+    uint32_t* dst = out32 + (o0 + j0) * 25u + lane;
 #pragma unroll
-    for (int it = 0; it < 25; ++it) {
-      const uint32_t w = lane + 32u * it;
-      if (w < nrec * 25u) dst[w] = v[it];
-    }
+    for (int r = 0; r < 32; ++r)
+      if (lane < 25u && (uint32_t)r < nrec) dst[r * 25] = v[r];
   }
 }
 

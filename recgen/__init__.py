@@ -19,6 +19,9 @@ Definitions (identical in the C and CUDA implementations):
   ``log2(i) mod 128``): uniform bytes, then bytes 0-5 replaced by entry
   ``t = floor(log2 i) mod 128`` (record 0: entry 0) of a seed-drawn table whose
   byte p of entry t is ``0x20 + mulhi32(h(t,p,4) >> 32, 95)``
+* variable-length key (Sec. 4: keys of different lengths, the longest l = 10,
+  padded with 0): ``L = 1 + mulhi32(h(i,12,5) >> 32, 10)`` uniform bytes, then
+  0x00 up to byte 10
 * duplicates: with probability d (``h(i,10,1) < floor(d*2^64)``) the key is the
   base key of record ``mulhi64(h(i,11,1), n)``
 * payload: 32 hex digits of i, 56 filler letters, CRLF
@@ -54,14 +57,14 @@ def h(seed: int, i: int, pos: int, stream: int) -> int:
 class KeySpec:
     """How the 10-byte keys of one record set are drawn."""
 
-    kind: str = "uniform"  # "uniform" | "zipf" | "prefix" (the paper's table-of-prefixes skew)
+    kind: str = "uniform"  # "uniform" | "zipf" | "prefix" (the paper's table-of-prefixes skew) | "varlen"
     s: float = 1.1  # Zipf exponent (kind == "zipf")
     dup: float = 0.0  # fraction of exact-duplicate keys
     seed: int = 1
 
     def tables(self):
         """(cum[94] uint64, perm[10*95] uint8, dup_thr) shared by both generators."""
-        if self.kind in ("uniform", "prefix"):
+        if self.kind in ("uniform", "prefix", "varlen"):
             cum = np.full(94, _M64, dtype=np.uint64)
             perm = np.tile(np.arange(95, dtype=np.uint8), 10)
         elif self.kind == "zipf":
@@ -88,7 +91,7 @@ class KeySpec:
 
     @property
     def kind_code(self) -> int:
-        return {"uniform": 0, "zipf": 1, "prefix": 2}[self.kind]
+        return {"uniform": 0, "zipf": 1, "prefix": 2, "varlen": 3}[self.kind]
 
 
 _cpu = None

@@ -14,8 +14,10 @@
  *            skew, the shape of the paper's skewed data, Sec. 7.1) uniform bytes
  *            whose first 6 are replaced by entry floor(log2 i) mod 128 of a table
  *            of 128 printable 6-byte prefixes (entry t, byte p: uniform from
- *            h(t,p,4); record 0 takes entry 0); with probability d the whole key
- *            is a copy of another record's base key
+ *            h(t,p,4); record 0 takes entry 0), or (variable length, Sec. 4) a key
+ *            of L = 1 + mulhi32(h(i,12,5) >> 32, 10) uniform bytes padded with
+ *            0x00 to 10 bytes; with probability d the whole key is a copy of
+ *            another record's base key
  *   [10,42)  32 upper-case hex digits of i (128-bit, big-endian, zero padded)
  *   [42,98)  filler 'A' + ((i + j) mod 26), j = 0..55
  *   [98,100) "\r\n"
@@ -48,7 +50,7 @@ static inline uint64_t rg_mulhi64(uint64_t a, uint64_t b) {
 typedef struct {
   uint64_t seed;
   uint64_t n_total;     /* size of the record set (duplicate sources are drawn from it) */
-  int kind;             /* 0 uniform, 1 zipf, 2 prefix skew */
+  int kind;             /* 0 uniform, 1 zipf, 2 prefix skew, 3 variable length */
   uint64_t dup_thr;     /* duplicate if h(i,10,1) < dup_thr (0 = none) */
   const uint64_t* cum;  /* 94 cumulative Zipf thresholds (fixed point, 2^64 scale) */
   const uint8_t* perm;  /* 10 x 95 per-position permutation of ranks */
@@ -61,7 +63,11 @@ static inline uint8_t rg_key_byte(const rg_spec* s, uint64_t i, int pos) {
     const uint64_t t = i ? (uint64_t)(63 - __builtin_clzll(i)) & 127u : 0;
     return rg_uniform_byte(rg_h(s->seed, t, (uint64_t)pos, 4));
   }
-  if (s->kind == 0 || s->kind == 2) {
+  if (s->kind == 3) {
+    const uint64_t len = 1 + (((rg_h(s->seed, i, 12, 5) >> 32) * 10u) >> 32);
+    if ((uint64_t)pos >= len) return 0;
+  }
+  if (s->kind == 0 || s->kind == 2 || s->kind == 3) {
     uint64_t u = rg_h(s->seed, i, (uint64_t)pos, 0) >> 32;
     return (uint8_t)(0x20 + ((u * 95u) >> 32));
   }

@@ -36,7 +36,11 @@ __device__ __forceinline__ uint8_t key_byte(const Spec& s, const uint64_t* cum, 
     const uint64_t u = hrand(s.seed, t, (uint64_t)pos, 4) >> 32;
     return (uint8_t)(0x20 + ((u * 95u) >> 32));
   }
-  if (s.kind == 0 || s.kind == 2) {
+  if (s.kind == 3) {  // variable length: 1..10 uniform bytes, then 0x00
+    const uint64_t len = 1 + (((hrand(s.seed, i, 12, 5) >> 32) * 10u) >> 32);
+    if ((uint64_t)pos >= len) return 0;
+  }
+  if (s.kind == 0 || s.kind == 2 || s.kind == 3) {
     uint64_t u = hrand(s.seed, i, (uint64_t)pos, 0) >> 32;
     return (uint8_t)(0x20 + ((u * 95u) >> 32));
   }

@@ -19,6 +19,7 @@ SPECS = {
     "zipf11": recgen.KeySpec("zipf", s=1.1, dup=0.05, seed=3),
     "zipf13": recgen.KeySpec("zipf", s=1.3, dup=0.10, seed=5),
     "prefix": recgen.KeySpec("prefix", seed=8),  # the paper's table-of-prefixes skew (Sec. 7.1)
+    "varlen": recgen.KeySpec("varlen", seed=9),  # keys of 1-10 bytes padded with 0 (Sec. 4)
 }
 
 
@@ -126,7 +127,7 @@ def test_uniform_1M_64_partitions():
     assert oracle.validate(host, got) == 0
 
 
-@pytest.mark.parametrize("name", ["zipf11", "zipf13", "prefix"])
+@pytest.mark.parametrize("name", ["zipf11", "zipf13", "prefix", "varlen"])
 @pytest.mark.parametrize("balance,schedule", [(0, 0), (1, 1), (1, 0), (0, 1)])
 def test_skewed_sort_matches_oracle(name, balance, schedule):
     n, P, S, seed = 400_000, 256, 4000, 9
@@ -218,7 +219,7 @@ def test_unfitted_model_rejected():
     assert e.value.status == 6
 
 
-@pytest.mark.parametrize("name", ["zipf13", "prefix"])
+@pytest.mark.parametrize("name", ["zipf13", "prefix", "varlen"])
 def test_generator_twins_agree(name):
     n = 1_000_000
     spec = SPECS[name]
@@ -356,3 +357,29 @@ def test_partition_size_variance_radix_vs_models():
            "network": round(cv[elsar.MODEL_MLP], 4)})
     assert cv[elsar.MODEL_RMI] < 0.5 * cv[elsar.MODEL_RADIX]
     assert cv[elsar.MODEL_MLP] < cv[elsar.MODEL_RADIX]
+
+
+# ---------------------------------------------------------------- key fields shorter than 10 bytes (Sec. 4)
+@pytest.mark.parametrize("l", [3, 8, 9])
+def test_short_key_field_matches_oracle(l):
+    """key_bytes = l: the first l bytes are the key (the GPU masks the rest of
+    the field to 0 in the pair, the oracle pads with 0): the fitted model, the
+    fine bin of every record and the sorted output equal the oracle's."""
+    n, P, S, seed = 300_000, 64, 3000, 6
+    host = recgen.generate_cpu(n, SPECS["zipf11"])
+    p = elsar.Params(num_partitions=P, sample_size=S, seed=seed, key_bytes=l)
+    d_rec, ws, model = _fit(host, p, n)
+    log2B = _resolved_log2B(n, P)
+    B = 1 << log2B
+    pairs = torch.empty(n * 16, dtype=torch.uint8, device="cuda")
+    bin_off = torch.empty(B + 1, dtype=torch.int32, device="cuda")
+    part_off = torch.empty(P + 1, dtype=torch.int64, device="cuda")
+    elsar.partition(model, d_rec, n, p, pairs, bin_off, part_off, ws)
+    torch.cuda.synchronize()
+    with oracle.key_bytes(l):
+        want, det = oracle.sort(host, P, log2B, S=S, seed=seed, balance=1, want_detail=True)
+    bo = bin_off.cpu().numpy().view(np.uint32).astype(np.int64)
+    assert np.array_equal(np.diff(bo), det["bin_counts"].astype(np.int64))
+    assert np.array_equal(part_off.cpu().numpy().astype(np.uint64), det["part_off"])
+    got, _ = _sort_gpu(host, n, p)
+    assert np.array_equal(got, want)
