@@ -536,6 +536,8 @@ def run_cfg4(args, dev, stream):
         sp = elsar.sort(d_in, d_out, n, pp, ws=ws, stream=stream, stats=True)
         torch.cuda.synchronize()
         res[name] = {"value": round(n * RECORD / (ms / 1e3) / 1e9, 2), "unit": "GB/s", "ms": round(ms, 3),
+                     "passes_ms": {k: round(v, 3) for k, v in zip(("fit", "classify", "scan_cuts_items", "scatter",
+                                                                      "sort_gather"), st["pass_ms"])},
                      "model_used": ["rmi", "network", "radix"][st["model_used"]],
                      "fallback_reason": st["fallback_reason"], "fit_ms": round(st["pass_ms"][0], 3),
                      "imbalance_refined": round(st["max_partition"] * P / n, 4),

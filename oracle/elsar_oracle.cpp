@@ -587,11 +587,13 @@ int eo_sort_by_splitters(const uint8_t* in, uint64_t n, const uint64_t* t, uint3
 //   knots   from the sorted sample (seed), as the network was trained on it;
 //   check 1 (boundary)  F(T_0) < 1/16 and F(T_12) > 15/16 in FP32, else reason 1;
 //   check 2 (judge)     a held-out sample (seed + 1, S keys) put into J judge
-//                       buckets (groups of 2^(log2B - log2J) consecutive fine
-//                       bins; log2J the largest value <= log2B, at least 1, with
-//                       64 * 2^log2J <= S) by the RMI's fine bins and by the
-//                       network's splitters: the network's largest bucket may
-//                       not hold more keys than the RMI's, else reason 2;
+//                       buckets (log2J the largest value <= log2B, at least 1,
+//                       with 64 * 2^log2J <= S): by the RMI, bucket
+//                       floor(fine bin / 2^(log2B - log2J)); by the network, the
+//                       number of its J-resolution splitters (those of
+//                       min(J-1, floor(J F)), made non-decreasing) at or below
+//                       the key.  The network's largest bucket may not hold
+//                       more keys than the RMI's, else reason 2;
 //   check 3 (full data) the network's partitions of all n records (its
 //                       splitters, the configured cut rule): the largest may
 //                       not exceed 1.1 times the mean, else reason 3.
@@ -617,7 +619,6 @@ int eo_model_choice(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, u
   uint64_t knots[13];
   eo_mlp_knots(sample.data(), S, knots);
   std::vector<uint64_t> t(B);
-  eo_mlp_splitters(w, knots, log2B, t.data());
   // check 1: F at the first and last knot
   float phi[2 * 12], Fk[2];
   const uint64_t ends[2] = {knots[0], knots[12]};
@@ -628,10 +629,12 @@ int eo_model_choice(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, u
   while (log2J < log2B && (64ull << (log2J + 1)) <= S) ++log2J;
   const uint32_t J = 1u << log2J;
   eo_sample(in, n, S, seed + 1, held.data());
+  std::vector<uint64_t> tJ(J);
+  eo_mlp_splitters(w, knots, log2J, tJ.data());
   std::vector<uint64_t> hr(J, 0), hm(J, 0);
   for (uint64_t k = 0; k < S; ++k) {
     hr[fine_bin(rmi_cdf(m, held[k]), log2B) >> (log2B - log2J)]++;
-    hm[bin_by_splitters(t.data(), B, held[k]) >> (log2B - log2J)]++;
+    hm[bin_by_splitters(tJ.data(), J, held[k])]++;
   }
   const uint64_t mr = *std::max_element(hr.begin(), hr.end()), mm = *std::max_element(hm.begin(), hm.end());
   int reason = 0;
@@ -639,6 +642,7 @@ int eo_model_choice(const uint8_t* in, uint64_t n, uint32_t P, uint32_t log2B, u
   else if (!(skip & 2) && mm > mr) reason = 2;
   uint64_t maxpart = 0;
   if (reason == 0 && !(skip & 4)) {
+    eo_mlp_splitters(w, knots, log2B, t.data());
     std::vector<uint64_t> off(P + 1);
     eo_sort_by_splitters(in, n, t.data(), log2B, P, balance, nullptr, nullptr, nullptr, off.data(), nullptr, nullptr);
     for (uint32_t p = 0; p < P; ++p) maxpart = std::max<uint64_t>(maxpart, off[p + 1] - off[p]);

@@ -248,16 +248,18 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
   ta.stream = st;
   ta.launches = launches;
   if ((e = mlp_train(ta)) != cudaSuccess) return cuda_fail(e, "mlp train");
-  if ((e = mlp_splitters(w, T, r.log2B, mlp_t, st)) != cudaSuccess) return cuda_fail(e, "mlp splitters");
-  // held-out keys (seed + 1) classified by both splitter sets into J judge buckets
+  // held-out keys (seed + 1) put into J judge buckets: by the RMI's fine bins
+  // (floor(q / 2^(log2B - log2J))) and by the network's J-resolution splitters
+  // (its fine-bin splitters are computed only if it is kept)
   uint64_t* held = sorted == f.samp ? f.samp + r.S : f.samp;
   uint32_t log2J = 1;
   while (log2J < r.log2B && (64ull << (log2J + 1)) <= r.S) ++log2J;
   const uint32_t J = 1u << log2J;
   uint32_t* hj = at<uint32_t>(d_ws, L.judge);
+  if ((e = mlp_splitters(w, T, log2J, mlp_t, st)) != cudaSuccess) return cuda_fail(e, "mlp judge splitters");
   if ((e = sample_keys(f.records, n, r.S, r.seed + 1, f.km, held, st)) != cudaSuccess) return cuda_fail(e, "held-out");
   if ((e = judge_histogram(held, r.S, rmi_t, r.log2B, log2J, hj, st)) != cudaSuccess) return cuda_fail(e, "judge");
-  if ((e = judge_histogram(held, r.S, mlp_t, r.log2B, log2J, hj + J, st)) != cudaSuccess) return cuda_fail(e, "judge");
+  if ((e = judge_histogram(held, r.S, mlp_t, log2J, log2J, hj + J, st)) != cudaSuccess) return cuda_fail(e, "judge");
   // boundary check: F at the smallest and largest sample keys
   float* Fb = reinterpret_cast<float*>(hj + 2 * J);
   if ((e = mlp_eval(w, T, T, 13, Fb, st)) != cudaSuccess) return cuda_fail(e, "mlp eval");
@@ -277,7 +279,8 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
   if (!(r.skip & ELSAR_SKIP_BOUNDARY) && !boundary_ok) res->fallback = 1;
   else if (!(r.skip & ELSAR_SKIP_JUDGE) && res->judge_mlp_max > res->judge_rmi_max) res->fallback = 2;
   if (res->fallback == 0) {
-    // the network wins: its splitters become the active ones, the RMI's are kept as the alternate
+    // the network wins: its fine-bin splitters become the active ones, the RMI's are kept as the alternate
+    if ((e = mlp_splitters(w, T, r.log2B, mlp_t, st)) != cudaSuccess) return cuda_fail(e, "mlp splitters");
     uint64_t* tmp = at<uint64_t>(d_ws, L.swap);
     const size_t bytes = (size_t)8 << r.log2B;
     cudaMemcpyAsync(tmp, rmi_t, bytes, cudaMemcpyDeviceToDevice, st);

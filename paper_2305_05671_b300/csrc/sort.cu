@@ -3,9 +3,11 @@
 // bins (model sub-buckets) of one partition holding at most `cap` pairs.  One
 // CTA sorts an item in shared memory -- a counting sort on the leading bits of
 // the keys' base-95 encoding over the item's key range (a placement by value,
-// like the model's), every bucket of up to kRankMax pairs then finished by
-// ranking each pair against its bucket (the touch-up, one thread per pair),
-// longer buckets split again the same way by warps on their own key range --
+// like the model's); when that leaves many keys in buckets of kSplitMin or
+// more (skewed keys), a second counting pass splits those buckets on their
+// next bits; every bucket of up to kRankMax pairs is then finished by ranking
+// each pair against its bucket (the touch-up, one thread per pair), longer
+// buckets split again the same way by warps on their own key range --
 // and gathers the 100-byte records of the item, in order, straight into their
 // final place in the output, so the partitions come out concatenated with no
 // merge.  Items above `cap` pairs (heavy duplicate keys) take a multi-pass
@@ -15,7 +17,7 @@
 // (oversize items first) -- the GPU form of the paper's dynamic scheduling of
 // uneven partitions; PER_PARTITION = one launch per partition.
 //
-// Each CTA is warp-specialised: 8 sorter warps sort the next items in shared
+// Each CTA is warp-specialised: 8 sorter warps sort the next item in shared
 // memory while kGatherWarps gatherer warps move the records of earlier ones,
 // so that the sort's shared-memory work overlaps the gather's DRAM traffic.
 // The sorters hand each sorted item over as a list of record indices in a
@@ -36,7 +38,7 @@ constexpr int kWarps = kThreads / 32;
 #endif
 constexpr int kGatherWarps = ELSAR_GATHER_WARPS;  // gatherer warps (after the sorters)
 constexpr int kBlockThreads = kThreads + 32 * kGatherWarps;
-constexpr uint32_t kSlots = 3;      // hand-over ring between the sorters and the gatherers
+constexpr uint32_t kSlots = 2;      // hand-over ring between the sorters and the gatherers
 constexpr uint32_t kRankMax = 128;  // buckets up to this length are ranked inside the digit pass (the touch-up)
 
 // named barriers: 1 = the sorter group; FULL[b] = 2 + b and EMPTY[b] = 2 + kSlots + b over the
@@ -63,7 +65,7 @@ __device__ __forceinline__ void empty_wait(uint32_t b) {
   else if (b == 1) ELSAR_BAR("sync", 6);
   else ELSAR_BAR("sync", 7);
 }
-static_assert(kSlots == 3, "the barrier helpers above name three slots");
+static_assert(kSlots <= 3, "the barrier helpers above name up to three slots");
 
 // A sorted item handed from the sorters to the gatherers.
 struct Handoff {
@@ -79,7 +81,7 @@ struct Misc {
   Handoff ho[kSlots];
   uint64_t red[2][kWarps];
   uint64_t kmin, kmax;
-  uint32_t nlong, next_long;
+  uint32_t nlong, next_long, nsplit;
   uint32_t stk_top[kWarps];
   uint32_t item;
   uint64_t split[2];
@@ -95,6 +97,8 @@ struct Tile {
   uint32_t* longs; // cap/kRankMax + 1 long runs of the first digit pass
   uint32_t* stk;   // kWarps x (cap/kRankMax + 1) refinement stacks
   uint32_t* idx;   // kSlots x cap: record indices of the items handed to the gatherers
+  uint16_t* dig2;  // cap: second-pass slot of each position
+  uint16_t* sb;    // cap: second-pass slot of each placed element
   uint64_t* enc;   // cap: base-95 encodings of the tile's keys (computed once per item)
   uint32_t stk_cap, cap;
   Misc* ms;
@@ -309,6 +313,10 @@ __device__ void warp_refine(const Tile& t, uint32_t s0, uint32_t len0) {
 // (hi, lo) order.  First digit pass block-wide over the whole tile, its short
 // buckets ranked in place by all threads, then the long runs are finished by
 // warps in parallel.
+// buckets of the first digit pass with this many elements or more are split
+// by a second counting pass when they hold at least 1/8 of the tile
+constexpr uint32_t kSplitMin = 8;
+
 __device__ void tile_sort(const Tile& t, uint32_t m) {
   Misc& ms = *t.ms;
   if (m <= 1) {
@@ -336,6 +344,7 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
   if (threadIdx.x == 0) {
     ms.nlong = 0;
     ms.next_long = 0;
+    ms.nsplit = 0;
   }
   sorter_sync();
   for (uint32_t j = threadIdx.x; j < m; j += kThreads)
@@ -344,8 +353,13 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
   {
     const uint32_t per = (D + kThreads - 1) / kThreads;
     const uint32_t b = min(D, threadIdx.x * per), e = min(D, b + per);
-    uint32_t local = 0;
-    for (uint32_t d = b; d < e; ++d) local += t.cnt[d];
+    uint32_t local = 0, big = 0;
+    for (uint32_t d = b; d < e; ++d) {
+      const uint32_t c = t.cnt[d];
+      local += c;
+      big += c >= kSplitMin ? c : 0u;
+    }
+    if (big) atomicAdd(&ms.nsplit, big);  // elements in buckets of kSplitMin or more
     uint32_t run = block_scan_excl(local, ms.wsum);
     for (uint32_t d = b; d < e; ++d) {
       const uint32_t c = t.cnt[d];
@@ -359,19 +373,79 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
     t.perm[pos] = (uint16_t)j;
   }
   sorter_sync();
-  // buckets up to kRankMax ranked in place (every element by its own thread)
-  for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
-    const uint32_t d = (uint32_t)((sel_key(t, t.perm[pos], sel) - kmin) >> shift);
-    place_ranked(t, pos, d ? t.cnt[d - 1] : 0, t.cnt[d]);
+  if (ms.nsplit * 8 >= m) {
+    // second counting pass: an element of a bucket [rs, rs + len) of kSplitMin or
+    // more goes to slot rs + sub, sub the next lb = floor(log2 len) bits of its key
+    // below the bucket's digit (2^lb <= len, so the slots stay inside the bucket);
+    // an element of a smaller bucket goes to slot rs.  Slots of different buckets
+    // never mix, so one plain exclusive scan over the tile gives every slot its
+    // final start, and a bucket's slots start at rs.
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
+      const uint64_t key = sel_key(t, t.perm[pos], sel);
+      const uint32_t d = (uint32_t)((key - kmin) >> shift);
+      const uint32_t rs = d ? t.cnt[d - 1] : 0, len = t.cnt[d] - rs;
+      uint32_t x = rs;
+      if (len >= kSplitMin) {
+        const uint32_t lb = 31 - __clz(len);
+        const uint64_t local = (key - kmin) - ((uint64_t)d << shift);
+        x = rs + (uint32_t)(shift >= lb ? local >> (shift - lb) : local);
+      }
+      t.dig2[pos] = (uint16_t)x;
+    }
+    sorter_sync();
+    for (uint32_t x = threadIdx.x; x < m; x += kThreads) t.cnt[x] = 0;
+    sorter_sync();
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) atomicAdd(t.cnt + t.dig2[pos], 1u);
+    sorter_sync();
+    {
+      const uint32_t per = (m + kThreads - 1) / kThreads;
+      const uint32_t b = min(m, threadIdx.x * per), e = min(m, b + per);
+      uint32_t local = 0;
+      for (uint32_t x = b; x < e; ++x) local += t.cnt[x];
+      uint32_t run = block_scan_excl(local, ms.wsum);
+      for (uint32_t x = b; x < e; ++x) {
+        const uint32_t c = t.cnt[x];
+        t.cnt[x] = run;
+        run += c;
+      }
+    }
+    sorter_sync();
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
+      const uint32_t x = t.dig2[pos];
+      const uint32_t np = atomicAdd(t.cnt + x, 1u);
+      t.perm2[np] = t.perm[pos];
+      t.sb[np] = (uint16_t)x;
+    }
+    sorter_sync();
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) t.perm[pos] = t.perm2[pos];
+    sorter_sync();
+    // slot x now holds [cnt[x-1], cnt[x]); rank inside slots of up to kRankMax
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
+      const uint32_t x = t.sb[pos];
+      place_ranked(t, pos, x ? t.cnt[x - 1] : 0, t.cnt[x]);
+    }
+    sorter_sync();
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) t.perm[pos] = t.perm2[pos];
+    for (uint32_t x = threadIdx.x; x < m; x += kThreads) {
+      const uint32_t s0 = x ? t.cnt[x - 1] : 0, len = t.cnt[x] - s0;
+      if (len > kRankMax) t.longs[atomicAdd(&ms.nlong, 1u)] = (s0 << 16) | len;
+    }
+    sorter_sync();
+  } else {
+    // buckets up to kRankMax ranked in place (every element by its own thread)
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
+      const uint32_t d = (uint32_t)((sel_key(t, t.perm[pos], sel) - kmin) >> shift);
+      place_ranked(t, pos, d ? t.cnt[d - 1] : 0, t.cnt[d]);
+    }
+    sorter_sync();
+    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) t.perm[pos] = t.perm2[pos];
+    for (uint32_t d = threadIdx.x; d < D; d += kThreads) {
+      const uint32_t s = d ? t.cnt[d - 1] : 0, e = t.cnt[d];
+      const uint32_t len = e - s;
+      if (len > kRankMax) t.longs[atomicAdd(&ms.nlong, 1u)] = (s << 16) | len;
+    }
+    sorter_sync();
   }
-  sorter_sync();
-  for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) t.perm[pos] = t.perm2[pos];
-  for (uint32_t d = threadIdx.x; d < D; d += kThreads) {
-    const uint32_t s = d ? t.cnt[d - 1] : 0, e = t.cnt[d];
-    const uint32_t len = e - s;
-    if (len > kRankMax) t.longs[atomicAdd(&ms.nlong, 1u)] = (s << 16) | len;
-  }
-  sorter_sync();
   const uint32_t lane = threadIdx.x & 31;
   for (;;) {
     uint32_t r = 0;
@@ -604,6 +678,10 @@ __device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
   p += (size_t)kWarps * t.stk_cap * 4;
   t.idx = reinterpret_cast<uint32_t*>(p);
   p += (size_t)kSlots * cap * 4;
+  t.dig2 = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * 2;
+  t.sb = reinterpret_cast<uint16_t*>(p);
+  p += (size_t)cap * 2;
   p = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(p) + 15) & ~(uintptr_t)15);
   t.enc = reinterpret_cast<uint64_t*>(p);
   p += (size_t)cap * 8;
@@ -661,7 +739,7 @@ __global__ void part_items_kernel(const uint32_t* cuts, const uint32_t* item_of_
 
 size_t sort_smem_bytes(uint32_t cap) {
   const size_t stk = (size_t)(cap / kRankMax + 1) * 4;
-  return (size_t)cap * (sizeof(Pair) + 4 + 2 + 2 + kSlots * 4 + 8) + stk * (1 + kWarps) + 32 + sizeof(Misc);
+  return (size_t)cap * (sizeof(Pair) + 4 + 2 + 2 + kSlots * 4 + 8 + 4) + stk * (1 + kWarps) + 32 + sizeof(Misc);
 }
 
 cudaError_t prepare_sort_kernel(uint32_t cap) {
