@@ -34,7 +34,7 @@ namespace {
 constexpr int kThreads = 256;  // sorter threads (warps 0-7)
 constexpr int kWarps = kThreads / 32;
 #ifndef ELSAR_GATHER_WARPS
-#define ELSAR_GATHER_WARPS 4
+#define ELSAR_GATHER_WARPS 5
 #endif
 constexpr int kGatherWarps = ELSAR_GATHER_WARPS;  // gatherer warps (after the sorters)
 constexpr int kBlockThreads = kThreads + 32 * kGatherWarps;
