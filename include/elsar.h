@@ -137,8 +137,10 @@ size_t elsar_model_size(uint64_t n, const elsar_params* p);
  * base 95 (Sec. 4), sorted, an RMI of linear models fitted on the sorted
  * sample, then the B-1 fine-bin splitters of the model (the smallest key
  * encoding whose fine bin floor(B*F) is at least q).  Writes d_model
- * (elsar_model_size bytes).  Reads a few bytes back per RMI level, so it
- * synchronises `stream`.
+ * (elsar_model_size bytes).  Asynchronous for the RMI and RADIX kinds (the
+ * RMI's levels run in a device-side loop: a graph whose while-node repeats
+ * them until a level has no children); the network reads its judge counts
+ * back, so model_kind MLP synchronises `stream`.
  * Errors: EINVAL (null/misaligned pointers, bad params, n == 0), ENOMEM
  * (buffers too small), EUNSUPPORTED (n >= 2^32), ECUDA.
  */
@@ -178,7 +180,11 @@ elsar_status elsar_sort_partitions(const void* d_records, uint64_t n, const elsa
  * The whole method on one record set resident in device memory:
  * elsar_fit_model, elsar_partition and elsar_sort_partitions back to back,
  * with their buffers carved from d_ws.  d_out receives the sorted records.
- * Synchronises `stream` (model fitting reads back level sizes).
+ * With stats == NULL and model_kind RMI or RADIX the call is asynchronous:
+ * it enqueues the work on `stream` and returns; a device-side wait that gave
+ * up (ELSAR_ETIMEOUT) is then kept in the workspace and reported by
+ * elsar_wait.  With stats, or with model_kind MLP (its checks read counts
+ * back), it synchronises `stream` and reports ELSAR_ETIMEOUT itself.
  * Errors: as the three calls.
  */
 elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_params* p, void* d_ws,
@@ -187,10 +193,23 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
 /*
  * End-to-end convenience: host records in, host records out.  Copies
  * h_in to d_in, sorts into d_out, copies d_out to h_out, all on `stream`
- * (pinned host buffers make the copies asynchronous DMA).  Synchronises.
+ * (pinned host buffers make the copies asynchronous DMA).  Synchronises
+ * and reports like elsar_wait.
  */
 elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_in,
                              void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
+
+/*
+ * Status of the asynchronous calls on workspace d_ws (ws_bytes >= 140, the
+ * control words that open every workspace): synchronises `stream`, then
+ * returns ELSAR_ETIMEOUT if a device-side bounded wait gave up in any
+ * elsar_sort call on this workspace since the last check (that call's output
+ * is not valid; later calls are unaffected: each clears its own status at
+ * its start), and clears the report; ELSAR_OK otherwise.  A workspace no call
+ * has used yet reports ELSAR_OK.  Errors: EINVAL (null, not 256-byte aligned
+ * or too small), ECUDA.
+ */
+elsar_status elsar_wait(void* d_ws, size_t ws_bytes, elsar_stream_t stream);
 
 /*
  * Out of core: n records in pinned host memory (h_in, allocated with
@@ -337,7 +356,8 @@ elsar_status elsar_mlp_adam(float* d_w, const float* d_grad, float* d_m, float* 
  * array and it keeps the previous call's contents (each call clears what
  * must start at zero): calls that can overlap on the GPU -- on different
  * streams, or from different threads -- race on it and must be serialised by
- * the caller.  Synchronises `stream` like elsar_sort.
+ * the caller.  Synchronises `stream` and reports a device-side timeout of its
+ * own sort (elsar_sort, then elsar_wait on the scratch).
  */
 elsar_status elsar_sort_noalloc(const void* d_in, void* d_out, uint64_t n, const elsar_params* p,
                                 elsar_stream_t stream);

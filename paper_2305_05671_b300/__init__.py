@@ -101,6 +101,7 @@ def lib():
             "elsar_sort_partitions": (ctypes.c_int, [P, U64, PP, P, P, P, P, SZ, P]),
             "elsar_sort": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_Stats)]),
             "elsar_sort_host": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
+            "elsar_wait": (ctypes.c_int, [P, SZ, P]),
             "elsar_sort_noalloc": (ctypes.c_int, [P, P, U64, PP, P]),
             "elsar_ooc_min_workspace": (SZ, [U64, PP]),
             "elsar_selftest_bounded_wait": (ctypes.c_int, [P, P, U64, P, ctypes.POINTER(ctypes.c_uint32 * 3)]),
@@ -195,13 +196,19 @@ def sort_partitions(d_records, n: int, p: Params, d_pairs, d_bin_offsets, d_out,
 
 
 def sort(d_in, d_out, n: int, p: Params | None = None, ws=None, stream=None, stats: bool = False):
-    """Sort n records of d_in into d_out (both CUDA uint8 tensors); returns a stats dict if asked."""
+    """Sort n records of d_in into d_out (both CUDA uint8 tensors); returns a stats dict if asked.
+
+    Without stats the call is asynchronous on `stream` (wait(ws) reports a device-side timeout); with a
+    workspace of its own (ws None) it waits, so that the workspace outlives the work."""
     p = p or Params()
-    if ws is None:
+    own_ws = ws is None
+    if own_ws:
         ws = alloc_workspace(n, p, device=d_in.device)
     st = _Stats() if stats else None
     _check(lib().elsar_sort(_ptr(d_in), _ptr(d_out), n, ctypes.byref(p.c()), _ptr(ws), _nbytes(ws), _stream(stream),
                             ctypes.byref(st) if st is not None else None))
+    if own_ws and st is None and n:
+        wait(ws, stream)
     if st is None:
         return None
     return dict(pass_ms=list(st.pass_ms)[:5], launches=st.launches, num_items=st.num_items,
@@ -209,6 +216,12 @@ def sort(d_in, d_out, n: int, p: Params | None = None, ws=None, stream=None, sta
                 max_bin=st.max_bin, model_used=st.model_used, fallback_reason=st.fallback_reason,
                 judge_buckets=st.judge_buckets, judge_rmi_max=st.judge_rmi_max, judge_mlp_max=st.judge_mlp_max,
                 F_first_knot=st.F_first_knot, F_last_knot=st.F_last_knot)
+
+
+def wait(ws, stream=None):
+    """Wait for `stream`; raise ElsarError(ELSAR_ETIMEOUT) if a device-side wait gave up in an asynchronous
+    sort on workspace ws since the last check."""
+    _check(lib().elsar_wait(_ptr(ws), _nbytes(ws), _stream(stream)))
 
 
 def sort_noalloc(d_in, d_out, n: int, p: Params | None = None, stream=None):

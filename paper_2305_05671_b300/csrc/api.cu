@@ -217,7 +217,7 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
     return ELSAR_OK;
   }
   const uint64_t* sorted = nullptr;
-  e = fit_rmi(f, &res->nodes, &sorted);
+  e = fit_rmi(f, &sorted);
   if (e != cudaSuccess) return cuda_fail(e, "fit");
   res->kind = ELSAR_MODEL_RMI;
   res->fallback = 0;
@@ -289,9 +289,10 @@ elsar_status do_fit(const void* d_records, uint64_t n, const Resolved& r, void* 
     if ((e = build_fine_lut(rmi_t, r.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut), st)) != cudaSuccess)
       return cuda_fail(e, "lut");
     res->kind = ELSAR_MODEL_MLP;
+    *launches += 2 + kFineLutLaunches;
   }
   if ((e = set_model_kind(d_model, res->kind, res->fallback, st)) != cudaSuccess) return cuda_fail(e, "header");
-  *launches += 6;
+  *launches += 7;  // judge splitters (2), held-out sample, two histograms, F at the knots, header
   return ELSAR_OK;
 }
 
@@ -373,6 +374,19 @@ elsar_status do_sort_partitions(const void* d_records, uint64_t n, const Resolve
 
 // Device-side failures (a bounded wait that gave up) are latched in the
 // workspace status word; read it back (synchronises the stream).
+// A call that does not read its status word back ORs it into the sticky
+// word for elsar_wait (the tag marks the sticky word valid: a fresh
+// workspace holds anything).
+__global__ void note_status_kernel(uint32_t* ctrl) {
+  uint64_t* tag = reinterpret_cast<uint64_t*>(ctrl + kStickyTag);
+  if (*tag != kStickyMagic) {
+    *tag = kStickyMagic;
+    ctrl[kStickyStatus] = ctrl[kStatusWord];
+  } else {
+    ctrl[kStickyStatus] |= ctrl[kStatusWord];
+  }
+}
+
 elsar_status device_status(void* d_ws, const Layout& L, cudaStream_t st) {
   uint32_t w = 0;
   cudaError_t e = cudaMemcpyAsync(&w, at<uint32_t>(d_ws, L.ctrl) + kStatusWord, 4, cudaMemcpyDeviceToHost, st);
@@ -536,7 +550,14 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
     s = do_sort_partitions(d_in, n, r, at<void>(d_ws, L.pairsB), at<uint32_t>(d_ws, L.bin_off), d_out, d_ws, L, st,
                            &launches, ev[5]);
   if (s == ELSAR_OK && stats) cudaEventRecord(ev[6], st);
-  if (s == ELSAR_OK) s = device_status(d_ws, L, st);
+  if (s == ELSAR_OK) {
+    if (stats) {
+      s = device_status(d_ws, L, st);
+    } else {  // no round trip: the status word waits in the sticky word for elsar_wait
+      note_status_kernel<<<1, 1, 0, st>>>(at<uint32_t>(d_ws, L.ctrl));
+      ++launches;
+    }
+  }
   if (s == ELSAR_OK && stats) {
     cudaError_t e = cudaEventSynchronize(ev[6]);
     if (e != cudaSuccess) {
@@ -553,7 +574,11 @@ elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_p
       stats->pass_ms[3] = ms(3, 4);
       stats->pass_ms[4] = ms(5, 6);
       stats->launches = launches;
-      stats->model_nodes = fr.nodes;
+      ModelHeader mh = {};
+      cudaMemcpy(&mh, model, sizeof mh, cudaMemcpyDeviceToHost);
+      stats->model_nodes = mh.num_nodes;
+      // the RMI's device loop was counted as one graph launch: count its kernels (six per level)
+      if (r.kind != ELSAR_MODEL_RADIX) stats->launches += 6 * mh.levels - 1;
       stats->model_used = fr.kind;
       stats->fallback_reason = fr.fallback;
       stats->judge_buckets = fr.judge_J;
@@ -594,8 +619,25 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
   if (s != ELSAR_OK) return s;
   if (n && (e = cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
     return cuda_fail(e, "copy out");
-  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(e, "sync");
-  return ELSAR_OK;
+  return n ? elsar_wait(d_ws, ws_bytes, stream) : ELSAR_OK;  // synchronises
+}
+
+elsar_status elsar_wait(void* d_ws, size_t ws_bytes, elsar_stream_t stream) {
+  g_err.clear();
+  if (!d_ws || !aligned(d_ws, 256) || ws_bytes < (kStickyStatus + 1) * 4)
+    return fail(ELSAR_EINVAL, "null, misaligned or too small workspace");
+  cudaStream_t st = (cudaStream_t)stream;
+  uint32_t w[3] = {};
+  uint32_t* ctrl = static_cast<uint32_t*>(d_ws);  // the control words open the workspace
+  cudaError_t e = cudaMemcpyAsync(w, ctrl + kStickyTag, sizeof w, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "check");
+  const uint64_t tag = ((uint64_t)w[1] << 32) | w[0];
+  if (tag != kStickyMagic || !w[2]) return ELSAR_OK;
+  e = cudaMemsetAsync(ctrl + kStickyStatus, 0, 4, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "check");
+  return fail(ELSAR_ETIMEOUT, "a device-side wait timed out in an earlier call (status word %u)", w[2]);
 }
 
 // ---------------------------------------------------------------- out of core

@@ -354,18 +354,18 @@ cudaError_t enqueue(elsar_batch& b, cudaStream_t st) {
   la.sums = at<uint64_t>(ws, L.sums);
   la.fc = at<uint32_t>(ws, L.fc);
   la.ctrl = at<uint32_t>(ws, L.ctrl);
-  la.host_sync = false;
+  la.device_loop = false;
   la.stream = st;
   la.launches = &launches;
-  uint32_t nn = 0, lv = 0;
-  cudaError_t e = build_rmi_levels(la, &nn, &lv);
+  cudaError_t e = build_rmi_levels(la);
   if (e != cudaSuccess) return e;
   // 3. each set's splitters in its own range of the common bin space
   uint64_t* t = at<uint64_t>(ws, L.t);
-  if ((e = splitters_batch(la.nodes, K, at<uint32_t>(ws, L.log2B), at<uint64_t>(ws, L.tbase), L.B_total, t, st)) !=
-      cudaSuccess)
+  // (the bins of the sample points in the sums' place)
+  if ((e = splitters_batch(la.nodes, K, la.sets, at<uint32_t>(ws, L.log2B), at<uint64_t>(ws, L.tbase), L.B_total, x, S,
+                           la.pnode, reinterpret_cast<uint32_t*>(la.sums), t, st)) != cudaSuccess)
     return e;
-  ++launches;
+  launches += 2;
   // 4. classify, scan, scatter, work items
   BatchPartArgs pa = {};
   pa.ins = at<const uint8_t* const>(ws, L.ins);

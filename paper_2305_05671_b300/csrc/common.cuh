@@ -10,6 +10,7 @@ constexpr int kRecord = 100;
 constexpr uint64_t kEncTop = 630249409724609375ull;  // 95^9: one past the largest 9-character encoding
 constexpr uint32_t kModelMagic = 0x52534C45u;        // "ELSR"
 constexpr uint32_t kSettled = 0xFFFFFFFFu;           // sample point whose RMI node is already a leaf
+constexpr uint32_t kSettledBit = 0x80000000u;        // settled point: this bit | the index of its leaf
 constexpr int kCoarse = 4096;                        // splitters kept in shared memory for classification
 
 // 16-byte sort pair (the paper's pointer-only record, Sec. 3.3): ordering by
@@ -136,13 +137,17 @@ constexpr uint32_t kLutL1Words = 4;    // words of a level-1 entry
 constexpr uint32_t kLutDense = 4;      // cells with more splitters get a level-2 split
 constexpr uint32_t kLutMaxBits = 14;   // at most 2^14 sub-cells per cell
 constexpr uint32_t kLutOversplit = 2;  // sub-cells = 4 x the cell's splitters rounded up to a power of two
+constexpr uint32_t kLutWarpBits = 10;  // cells of up to 2^10 sub-cells are filled by a warp, larger ones by a block
 // Level-2 capacity for 2^log2B splitters: a dense cell with cnt splitters
 // takes 2^nb + 1 < 8 cnt + 1 words and at most B/5 cells are dense, so
-// 8B + B/4 words hold every split; 256 more at the end hold the scan's block
-// totals while the index is built.
+// 8B + B/4 words hold every split.  While the index is built, the words
+// after those hold the list of cells with more than 2^kLutWarpBits sub-cells
+// (more than 256 splitters each, so at most B/256 of them; a count, then
+// the cells) and, in the last 256, the scan's block totals.
+inline size_t lut_big_words(uint32_t log2B) { return ((size_t)1 << log2B) / 256 + 2; }
 inline size_t lut_level2_words(uint32_t log2B) {
   const size_t B = (size_t)1 << log2B;
-  return 8 * B + B / 4 + 256;
+  return 8 * B + B / 4 + lut_big_words(log2B) + 256;
 }
 // words of the whole index (level 1 and level 2)
 inline size_t lut_words_for(uint32_t log2B) {
@@ -266,9 +271,12 @@ struct FitArgs {
 };
 
 // Level-by-level RMI construction over K trees at once (K record sets whose
-// sorted samples are concatenated; sets[k] gives each segment).  `host_sync`
-// reads the level sizes back (single-set path); otherwise a fixed number of
-// levels is launched and empty levels exit at once (capturable in a graph).
+// sorted samples are concatenated; sets[k] gives each segment).  `device_loop`
+// runs the levels in a graph whose while-node repeats them until a level has
+// no children (single-set path; no host round trip); otherwise a fixed number
+// of levels is launched and empty levels exit at once (capturable in a
+// caller's graph).  The level count ends in ctrl[kLevelNodes + 5], the node
+// count in ctrl[kLevelNodes + 3].
 struct RmiLevelsArgs {
   const uint64_t* x;  // concatenated sorted samples
   uint64_t S_total;
@@ -280,14 +288,16 @@ struct RmiLevelsArgs {
   uint64_t* sums;
   uint32_t* fc;
   uint32_t* ctrl;
-  bool host_sync;
+  bool device_loop;
   cudaStream_t stream;
   uint32_t* launches;
 };
-cudaError_t build_rmi_levels(const RmiLevelsArgs& a, uint32_t* nodes_out, uint32_t* levels_out);
-// Splitters of every set: set k's B_k = 1 << log2B[k] splitters at t + tbase[k], tree k rooted at node k.
-cudaError_t splitters_batch(const DNode* nodes, uint32_t K, const uint32_t* log2B, const uint64_t* tbase,
-                            uint64_t total_bins, uint64_t* t, cudaStream_t st);
+cudaError_t build_rmi_levels(const RmiLevelsArgs& a);
+// Splitters of every set: set k's B_k = 1 << log2B[k] splitters at t + tbase[k], tree k rooted at node k,
+// from the settled sample points (build_rmi_levels' x and pnode); pbin: S_total words of scratch.  Two launches.
+cudaError_t splitters_batch(const DNode* nodes, uint32_t K, const SetInfo* sets, const uint32_t* log2B,
+                            const uint64_t* tbase, uint64_t total_bins, const uint64_t* x, uint64_t S_total,
+                            const uint32_t* pnode, uint32_t* pbin, uint64_t* t, cudaStream_t st);
 
 uint64_t node_cap_for(uint64_t S, uint32_t T);
 
@@ -298,11 +308,14 @@ struct ModelLayout {
 ModelLayout model_layout(uint64_t S, uint32_t log2B, uint32_t T);
 inline size_t model_bytes_for(uint64_t S, uint32_t log2B, uint32_t T) { return model_layout(S, log2B, T).bytes; }
 
-// fits the RMI; *sorted_out = the buffer holding the sorted sample (a.samp or a.samp + S)
-cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sorted_out);
+// fits the RMI without a host round trip (the node and level counts are in
+// the model header); *sorted_out = the buffer holding the sorted sample
+// (a.samp or a.samp + S)
+cudaError_t fit_rmi(const FitArgs& a, const uint64_t** sorted_out);
 cudaError_t sample_keys(const uint8_t* records, uint64_t n, uint64_t S, uint64_t seed, const KeyMask& km, uint64_t* out,
                         cudaStream_t st);
-// builds both levels of the radix index (scratch: kFineLutCells words)
+// builds both levels of the radix index (kFineLutLaunches kernels)
+constexpr uint32_t kFineLutLaunches = 5;
 cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* lut, cudaStream_t st);
 cudaError_t set_model_kind(void* model, uint32_t kind, uint32_t fallback, cudaStream_t st);
 // no model: the equal-width (radix) splitters t_q = ceil(q 95^9 / B), their index and the header
@@ -438,8 +451,13 @@ enum Ctrl : int {
   kQueueHead = 2,
   kMaxBin = 3,
   kStatus = 4,
-  kLevelNodes = 8,  // fit: [8] level begin, [9] level end, [10] next level count, [11] total nodes, [12] overflow
+  kLevelNodes = 8,  // fit: [8] level begin, [9] level end, [10] next level count, [11] total nodes, [12] overflow,
+                    // [13] levels done
   kStatusWord = 16,
+  // words 0-31 are cleared at the start of every partition; these are not:
+  kStickyTag = 32,     // [32], [33]: kStickyMagic once the sticky word below is valid
+  kStickyStatus = 34,  // OR of the status words of the calls that did not read theirs back
 };
+constexpr uint64_t kStickyMagic = 0x53544b59454c5352ull;
 
 }  // namespace elsar

@@ -5,6 +5,9 @@
 // order the model definition fixes (this file is also built with
 // -fmad=false), so the fitted model is bit-identical wherever it is computed
 // in that order.  Least-squares sums are exact integers (order independent).
+#include <mutex>
+#include <vector>
+
 #include "common.cuh"
 #include "mlp.cuh"
 
@@ -41,12 +44,97 @@ __device__ __forceinline__ uint64_t local_u(const DNode& v, uint64_t x) {
   return x > v.base ? (x - v.base) >> v.shift : 0;
 }
 
-// router of an internal node: clamp(floor(fma(gamma, u, delta) * scale), 0, f-1)
-__device__ __forceinline__ uint32_t route(const DNode& v, uint64_t x) {
-  double t = __dmul_rn(__fma_rn(v.a, __ull2double_rn(local_u(v, x)), v.b), v.c);
+// router of an internal node: clamp(floor(fma(gamma, u, delta) * scale), 0, f-1),
+// a monotone function of the local coordinate u (gamma >= 0, scale > 0)
+__device__ __forceinline__ uint32_t route_u(const DNode& v, uint64_t u) {
+  double t = __dmul_rn(__fma_rn(v.a, __ull2double_rn(u), v.b), v.c);
   if (!(t > 0.0)) return 0;
   if (t >= __uint2double_rn(v.fanout)) return v.fanout - 1;
   return __double2uint_rz(t);
+}
+
+__device__ __forceinline__ uint32_t route(const DNode& v, uint64_t x) { return route_u(v, local_u(v, x)); }
+
+// Smallest u in (a, b] with f(u) >= q for a monotone f with f(a) < q <=
+// f(b): a gallop from the guess m (it only sets the start; m > b: none, the
+// middle is taken), then a bisection.  Every decision evaluates f exactly.
+template <class F>
+__device__ __forceinline__ uint64_t first_at_least(const F& f, uint64_t a, uint64_t b, uint32_t q, uint64_t m) {
+  if (m > b) m = a + ((b - a + 1) >> 1);
+  else if (m <= a) m = a + 1;
+  if (f(m) >= q) {  // gallop down from m
+    b = m;
+    for (uint64_t step = 1; b - a > 1; step <<= 1) {
+      const uint64_t t = b - a > step ? b - step : a + 1;
+      if (f(t) >= q) {
+        b = t;
+      } else {
+        a = t;
+        break;
+      }
+    }
+  } else {  // gallop up from m
+    a = m;
+    for (uint64_t step = 1; b - a > 1; step <<= 1) {
+      const uint64_t t = b - a > step ? a + step : b - 1;
+      if (f(t) >= q) {
+        b = t;
+        break;
+      }
+      a = t;
+    }
+  }
+  while (b - a > 1) {
+    const uint64_t mid = a + ((b - a) >> 1);
+    if (f(mid) >= q) b = mid;
+    else a = mid;
+  }
+  return b;
+}
+
+// first index i in [lo, hi) with at(i) >= key (hi if none) of a
+// non-decreasing sequence: a gallop from the guess g, then a bisection
+template <class A, class T>
+__device__ __forceinline__ uint64_t gallop_first(const A& arr, uint64_t lo, uint64_t hi, T key, uint64_t g) {
+  uint64_t a = lo, b = hi;  // the answer lies in [a, b]
+  if (lo < hi) {
+    if (g < lo) g = lo;
+    if (g > hi - 1) g = hi - 1;
+    if (arr(g) >= key) {
+      b = g;
+      for (uint64_t step = 1; b > lo; step <<= 1) {
+        const uint64_t i = b - lo > step ? b - step : lo;
+        if (arr(i) >= key) {
+          b = i;
+        } else {
+          a = i + 1;
+          break;
+        }
+      }
+    } else {
+      a = g + 1;
+      for (uint64_t step = 1; a < hi; step <<= 1) {
+        const uint64_t i = a + step - 1 < hi - 1 ? a + step - 1 : hi - 1;
+        if (arr(i) >= key) {
+          b = i;
+          break;
+        }
+        a = i + 1;
+      }
+    }
+  }
+  while (a < b) {
+    const uint64_t mid = (a + b) >> 1;
+    if (arr(mid) >= key) b = mid;
+    else a = mid + 1;
+  }
+  return a;
+}
+
+template <class T>
+__device__ __forceinline__ uint64_t gallop_lower_bound(const T* __restrict__ arr, uint64_t lo, uint64_t hi, T key,
+                                                       uint64_t g) {
+  return gallop_first([&](uint64_t i) { return arr[i]; }, lo, hi, key, g);
 }
 
 __device__ __forceinline__ void atomic_add_u128(uint64_t* p, u128 v) {
@@ -54,12 +142,6 @@ __device__ __forceinline__ void atomic_add_u128(uint64_t* p, u128 v) {
   unsigned long long old = atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)lo);
   if (old + lo < old) hi += 1;
   if (hi) atomicAdd(reinterpret_cast<unsigned long long*>(p + 1), (unsigned long long)hi);
-}
-
-__device__ __forceinline__ u128 shfl_down_u128(u128 v, int d) {
-  uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)v, d);
-  uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(v >> 64), d);
-  return ((u128)hi << 64) | lo;
 }
 
 // ------------------------------------------------------------------ sample
@@ -167,26 +249,6 @@ __device__ __forceinline__ uint32_t set_of_point(const SetInfo* sets, uint32_t K
   return lo;
 }
 
-__global__ void init_roots(DNode* nodes, uint32_t* pnode, const SetInfo* __restrict__ sets, uint32_t K,
-                           uint64_t S_total, uint32_t* ctrl) {
-  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t k = t0; k < K; k += stride) {
-    DNode r = {};
-    r.s = (uint32_t)sets[k].soff;
-    r.e = (uint32_t)(sets[k].soff + sets[k].S);
-    r.depth_set = (uint32_t)k << 8;
-    nodes[k] = r;
-  }
-  if (t0 == 0) {
-    ctrl[kLevelNodes + 0] = 0;
-    ctrl[kLevelNodes + 1] = K;
-    ctrl[kLevelNodes + 2] = 0;
-    ctrl[kLevelNodes + 3] = K;
-    ctrl[kLevelNodes + 4] = 0;
-  }
-  for (uint64_t j = t0; j < S_total; j += stride) pnode[j] = set_of_point(sets, K, j);
-}
-
 // per-node base and shift, read by every point of the node
 __device__ __forceinline__ void node_frame(const uint64_t* x, uint32_t s, uint32_t e, uint64_t* base, uint32_t* sh) {
   uint64_t b = x[s];
@@ -196,44 +258,206 @@ __device__ __forceinline__ void node_frame(const uint64_t* x, uint32_t s, uint32
   *sh = bits > 32 ? bits - 32 : 0;
 }
 
-// exact sums Su, Suu, Sur of each node of the level (u = local coordinate, r = local rank)
-__global__ void level_sums(const uint64_t* __restrict__ x, uint64_t S, const DNode* __restrict__ nodes,
-                           const uint32_t* __restrict__ pnode, uint64_t* sums, const uint32_t* ctrl) {
+// the roots (with their frames) and every point in its set's root
+__global__ void init_roots(const uint64_t* __restrict__ x, DNode* nodes, uint32_t* pnode,
+                           const SetInfo* __restrict__ sets, uint32_t K, uint64_t S_total, uint32_t* ctrl) {
+  const uint64_t t0 = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x, stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = t0; k < K; k += stride) {
+    DNode r = {};
+    r.s = (uint32_t)sets[k].soff;
+    r.e = (uint32_t)(sets[k].soff + sets[k].S);
+    r.depth_set = (uint32_t)k << 8;
+    if (r.e > r.s) node_frame(x, r.s, r.e, &r.base, &r.shift);
+    nodes[k] = r;
+  }
+  if (t0 == 0) {
+    ctrl[kLevelNodes + 0] = 0;
+    ctrl[kLevelNodes + 1] = K;
+    ctrl[kLevelNodes + 2] = 0;
+    ctrl[kLevelNodes + 3] = K;
+    ctrl[kLevelNodes + 4] = 0;
+    ctrl[kLevelNodes + 5] = 0;
+  }
+  for (uint64_t j = t0; j < S_total; j += stride) pnode[j] = set_of_point(sets, K, j);
+}
+
+__device__ __forceinline__ u128 shfl_u128(u128 v, int src) {
+  uint64_t lo = __shfl_sync(0xffffffffu, (uint64_t)v, src);
+  uint64_t hi = __shfl_sync(0xffffffffu, (uint64_t)(v >> 64), src);
+  return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ u128 shfl_up_u128(u128 v, int d) {
+  uint64_t lo = __shfl_up_sync(0xffffffffu, (uint64_t)v, d);
+  uint64_t hi = __shfl_up_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+  return ((u128)hi << 64) | lo;
+}
+
+__device__ __forceinline__ void add_node_sums(uint64_t* sums, uint32_t lv0, uint32_t v, uint64_t u, u128 uu, u128 ur) {
+  uint64_t* sm = sums + (uint64_t)(v - lv0) * 6;
+  atomicAdd(reinterpret_cast<unsigned long long*>(sm), (unsigned long long)u);
+  atomic_add_u128(sm + 2, uu);
+  atomic_add_u128(sm + 4, ur);
+}
+
+constexpr int kSumsWarpPoints = 256;                   // consecutive points per warp
+constexpr int kSumsBlockPoints = 8 * kSumsWarpPoints;  // per 256-thread block
+
+// sum over the warp, every lane gets the totals
+__device__ __forceinline__ void warp_sum3(uint64_t& u, u128& uu, u128& ur) {
+  for (int d = 16; d; d >>= 1) {
+    u += __shfl_xor_sync(0xffffffffu, u, d);
+    uu += ((u128)__shfl_xor_sync(0xffffffffu, (uint64_t)(uu >> 64), d) << 64) |
+          __shfl_xor_sync(0xffffffffu, (uint64_t)uu, d);
+    ur += ((u128)__shfl_xor_sync(0xffffffffu, (uint64_t)(ur >> 64), d) << 64) |
+          __shfl_xor_sync(0xffffffffu, (uint64_t)ur, d);
+  }
+}
+
+// Exact sums Su, Suu, Sur per node (u = the node's local coordinate, r = the
+// local rank), over the points of the level's nodes [lv0, lv1).  kRoute =
+// false: the sums of those nodes (the roots, before the first level).  kRoute
+// = true: every point of an internal node first moves to its child (a point
+// of a leaf settles: kSettledBit | the leaf), and the sums are the children's
+// (the next level, numbered from lv1, ranges and frames set by
+// level_init_next).
+// A node holds a contiguous range of the sorted points, so a warp walks a
+// run of consecutive points 32 at a time.  A step whose 32 points share the
+// run's node only adds into per-lane sums; any other step gathers the run
+// (a warp sum), sums the step per node segment (segmented shuffle scan),
+// adds the segments that end and carries the last one on.  The warps of a
+// block then merge their final carries, so a node that spans the block is
+// added once per block.  Integer sums: the order of the additions does not
+// matter.
+template <bool kRoute>
+__global__ void __launch_bounds__(256) level_sums(const uint64_t* __restrict__ x, uint64_t S, const DNode* nodes,
+                                                  uint32_t* pnode, uint64_t* sums, const uint32_t* ctrl) {
+  __shared__ uint32_t cv_sh[8];
+  __shared__ uint64_t cu_sh[8];
+  __shared__ u128 cuu_sh[8], cur_sh[8];
   const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
   if (lv0 >= lv1) return;
-  for (uint64_t k0 = blockIdx.x * (uint64_t)blockDim.x; k0 < S; k0 += (uint64_t)gridDim.x * blockDim.x) {
-    uint64_t k = k0 + threadIdx.x;
-    uint32_t v = k < S ? pnode[k] : kSettled;
-    u128 u = 0, uu = 0, ur = 0;
-    if (v != kSettled) {
-      uint32_t s = nodes[v].s, e = nodes[v].e;
-      uint64_t base;
-      uint32_t sh;
-      node_frame(x, s, e, &base, &sh);
-      uint64_t uv = (x[k] - base) >> sh;
-      u = uv;
-      uu = (u128)uv * uv;
-      ur = (u128)uv * (uint64_t)(k - s);
-    }
-    uint32_t v0 = __shfl_sync(0xffffffffu, v, 0);
-    if (__all_sync(0xffffffffu, v == v0) && v0 != kSettled) {
-      for (int d = 16; d; d >>= 1) {
-        u += shfl_down_u128(u, d);
-        uu += shfl_down_u128(uu, d);
-        ur += shfl_down_u128(ur, d);
+  const uint32_t ofs = kRoute ? lv1 : lv0;  // sums of node v at (v - ofs) * 6
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (uint64_t b0 = blockIdx.x * (uint64_t)kSumsBlockPoints; b0 < S; b0 += (uint64_t)gridDim.x * kSumsBlockPoints) {
+    const uint64_t c0 = b0 + (uint64_t)warp * kSumsWarpPoints;
+    const uint64_t c1 = c0 + kSumsWarpPoints < S ? c0 + kSumsWarpPoints : S;
+    uint32_t cv = kSettled;  // the run's node (warp-uniform)
+    bool spread = false;     // the run's sums: per lane (spread) or warp-uniform (cu, cuu, cur)
+    uint64_t cu = 0, lu = 0;
+    u128 cuu = 0, cur = 0, luu = 0, lur = 0;
+    for (uint64_t k0 = c0; k0 < c1; k0 += 32) {
+      const uint64_t k = k0 + lane;
+      uint32_t v = k < c1 ? pnode[k] : kSettled;
+      if (v < lv0 || v >= lv1) v = kSettled;  // settled in a leaf of an earlier level
+      if (kRoute && v != kSettled) {
+        const DNode& nd = nodes[v];
+        if (nd.fanout) {
+          const uint32_t ch = nd.child0 + route(nd, x[k]);
+          pnode[k] = ch;
+          v = ch;
+        } else {
+          pnode[k] = kSettledBit | v;
+          v = kSettled;
+        }
       }
-      if ((threadIdx.x & 31) == 0) {
-        uint64_t* sm = sums + (uint64_t)(v0 - lv0) * 6;
-        atomicAdd(reinterpret_cast<unsigned long long*>(sm), (unsigned long long)(uint64_t)u);
-        atomic_add_u128(sm + 2, uu);
-        atomic_add_u128(sm + 4, ur);
+      uint64_t u = 0;
+      u128 uu = 0, ur = 0;
+      if (v != kSettled) {
+        const DNode& c = nodes[v];
+        const uint64_t uv = (x[k] - c.base) >> c.shift;
+        u = uv;
+        uu = (u128)uv * uv;
+        ur = (u128)uv * (uint64_t)(k - c.s);
       }
-    } else if (v != kSettled) {
-      uint64_t* sm = sums + (uint64_t)(v - lv0) * 6;
-      atomicAdd(reinterpret_cast<unsigned long long*>(sm), (unsigned long long)(uint64_t)u);
-      atomic_add_u128(sm + 2, uu);
-      atomic_add_u128(sm + 4, ur);
+      const uint32_t v0 = __shfl_sync(0xffffffffu, v, 0);
+      const bool same = __all_sync(0xffffffffu, v == v0);
+      if (same && v0 == cv && cv != kSettled) {  // the run goes on
+        if (!spread) {
+          lu = lane == 0 ? cu : 0;
+          luu = lane == 0 ? cuu : 0;
+          lur = lane == 0 ? cur : 0;
+          spread = true;
+        }
+        lu += u;
+        luu += uu;
+        lur += ur;
+        continue;
+      }
+      if (spread) {  // gather the run
+        warp_sum3(lu, luu, lur);
+        cu = lu;
+        cuu = luu;
+        cur = lur;
+        spread = false;
+      }
+      if (cv != kSettled && cv != v0) {  // the run ends before this step
+        if (lane == 0) add_node_sums(sums, ofs, cv, cu, cuu, cur);
+        cv = kSettled;
+      }
+      if (same) {  // all settled, or one node that starts a run
+        if (v0 != kSettled) {
+          cv = v0;
+          spread = true;
+          lu = u;
+          luu = uu;
+          lur = ur;
+        }
+        continue;
+      }
+      if (cv != kSettled && lane == 0) {  // lane 0 holds node cv: the scan takes the carry from there
+        u += cu;
+        uu += cuu;
+        ur += cur;
+      }
+      for (int d = 1; d < 32; d <<= 1) {  // inclusive scan inside each run of equal v
+        const uint32_t vp = __shfl_up_sync(0xffffffffu, v, d);
+        const uint64_t up = __shfl_up_sync(0xffffffffu, u, d);
+        const u128 uup = shfl_up_u128(uu, d), urp = shfl_up_u128(ur, d);
+        if (lane >= (uint32_t)d && vp == v) {
+          u += up;
+          uu += uup;
+          ur += urp;
+        }
+      }
+      const uint32_t vn = __shfl_down_sync(0xffffffffu, v, 1);
+      if (lane != 31 && vn != v && v != kSettled) add_node_sums(sums, ofs, v, u, uu, ur);
+      cv = __shfl_sync(0xffffffffu, v, 31);
+      cu = __shfl_sync(0xffffffffu, u, 31);
+      cuu = shfl_u128(uu, 31);
+      cur = shfl_u128(ur, 31);
     }
+    if (spread) {
+      warp_sum3(lu, luu, lur);
+      cu = lu;
+      cuu = luu;
+      cur = lur;
+    }
+    if (lane == 0) {
+      cv_sh[warp] = cv;
+      cu_sh[warp] = cu;
+      cuu_sh[warp] = cuu;
+      cur_sh[warp] = cur;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {  // merge the warps' carries, a node once per run of equal carries
+      uint32_t mv = kSettled;
+      uint64_t mu = 0;
+      u128 muu = 0, mur = 0;
+      for (int w = 0; w < 8; ++w) {
+        if (cv_sh[w] != mv) {
+          if (mv != kSettled) add_node_sums(sums, ofs, mv, mu, muu, mur);
+          mv = cv_sh[w];
+          mu = 0;
+          muu = mur = 0;
+        }
+        mu += cu_sh[w];
+        muu += cuu_sh[w];
+        mur += cur_sh[w];
+      }
+      if (mv != kSettled) add_node_sums(sums, ofs, mv, mu, muu, mur);
+    }
+    __syncthreads();
   }
 }
 
@@ -282,9 +506,13 @@ __global__ void level_fit(const uint64_t* __restrict__ x, DNode* nodes, const ui
 
 constexpr int kScanThreads = 1024;
 
+constexpr int kScanChunks = 16;  // 32-fanout chunks per warp and tile
+
 // Single CTA: child numbering = exclusive scan of the split fanouts of the
-// level (coalesced tiles of kScanThreads with a running carry) and the node
-// budget check.  ctrl[kLevelNodes+2] = next level size (0 on overflow),
+// level and the node budget check.  A tile is kScanThreads x kScanChunks
+// fanouts; warp w scans chunks of 32 consecutive ones (coalesced) across its
+// 512-fanout part, then the warps' totals are scanned and a running carry
+// joins the tiles.  ctrl[kLevelNodes+2] = next level size (0 on overflow),
 // ctrl[kLevelNodes+4] = 1 when the budget forbids splitting this level.
 __global__ void __launch_bounds__(kScanThreads) level_scan(const uint32_t* __restrict__ fc, uint32_t* __restrict__ childoff,
                                                            uint64_t node_cap, uint32_t* ctrl) {
@@ -295,15 +523,22 @@ __global__ void __launch_bounds__(kScanThreads) level_scan(const uint32_t* __res
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry_sh = 0;
   __syncthreads();
-  for (uint32_t base = 0; base < cnt; base += kScanThreads) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t v = i < cnt ? fc[i] : 0;
-    uint32_t incl = v;
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-      if (lane >= (uint32_t)d) incl += y;
+  for (uint32_t base = 0; base < cnt; base += kScanThreads * kScanChunks) {
+    const uint32_t w0 = base + warp * 32 * kScanChunks;
+    uint32_t ex[kScanChunks], run = 0;  // exclusive offset inside the warp's part
+#pragma unroll
+    for (int j = 0; j < kScanChunks; ++j) {
+      const uint32_t i = w0 + j * 32 + lane;
+      const uint32_t v = i < cnt ? fc[i] : 0;
+      uint32_t incl = v;
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= (uint32_t)d) incl += y;
+      }
+      ex[j] = run + incl - v;
+      run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    if (lane == 31) wsum[warp] = incl;
+    if (lane == 0) wsum[warp] = run;
     __syncthreads();
     if (warp == 0) {
       const uint32_t w = wsum[lane];
@@ -315,10 +550,14 @@ __global__ void __launch_bounds__(kScanThreads) level_scan(const uint32_t* __res
       wsum[lane] = wi - w;
     }
     __syncthreads();
-    const uint32_t carry = carry_sh;
-    if (i < cnt) childoff[i] = carry + wsum[warp] + incl - v;
+    const uint32_t carry = carry_sh, off = carry + wsum[warp];
+#pragma unroll
+    for (int j = 0; j < kScanChunks; ++j) {
+      const uint32_t i = w0 + j * 32 + lane;
+      if (i < cnt) childoff[i] = off + ex[j];
+    }
     __syncthreads();
-    if (threadIdx.x == kScanThreads - 1) carry_sh = carry + wsum[warp] + incl;
+    if (threadIdx.x == kScanThreads - 1) carry_sh = off + run;
     __syncthreads();
   }
   if (threadIdx.x == 0) {
@@ -369,154 +608,237 @@ __global__ void level_finalize(DNode* nodes, const uint32_t* __restrict__ fc, co
   }
 }
 
-// Records of the next level zeroed with their sums (level_route sets ranges,
-// depth and set).
-__global__ void level_init_next(DNode* nodes, uint64_t* sums, const uint32_t* ctrl) {
-  const uint32_t lv1 = ctrl[kLevelNodes + 1], next = ctrl[kLevelNodes + 2];
-  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w < next; w += gridDim.x * blockDim.x) {
+// first point k of internal node nd (nd.e if none) with route(nd, x[k]) >= cc:
+// routing is monotone in the sorted points
+__device__ __forceinline__ uint32_t first_routed(const uint64_t* __restrict__ x, const DNode& nd, uint32_t cc) {
+  uint32_t lo = nd.s, hi = nd.e;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (route(nd, x[mid]) >= cc) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// The nodes of the next level, each by one thread, with their sums zeroed:
+// child w finds its parent (the last node of the level whose first child is
+// <= w), its point range (the first point its parent routes to it, up to
+// the next child's first) and its frame.
+__global__ void level_init_next(DNode* nodes, uint64_t* sums, const uint32_t* __restrict__ childoff,
+                                const uint64_t* __restrict__ x, const uint32_t* ctrl) {
+  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1], next = ctrl[kLevelNodes + 2];
+  const uint32_t cnt = lv1 - lv0;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nw = (gridDim.x * blockDim.x) >> 5;
+  // a warp owns 31 consecutive children; lane 31 finds the start of the
+  // next one, which ends lane 30's child, so every lane searches once
+  for (uint32_t w0 = gw * 31; w0 < next; w0 += nw * 31) {
+    const uint32_t w = w0 + lane;
+    const bool act = w < next;
+    DNode nd = {};
+    uint32_t cc = 0, s = 0;
+    if (act) {
+      uint32_t lo = 0, hi = cnt - 1;
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (childoff[mid] <= w) lo = mid;
+        else hi = mid - 1;
+      }
+      nd = nodes[lv0 + lo];
+      cc = w - childoff[lo];
+      s = first_routed(x, nd, cc);
+    }
+    const uint32_t s_next = __shfl_down_sync(0xffffffffu, s, 1);
+    if (!act || lane == 31) continue;
     DNode c = {};
+    c.s = s;
+    // the end is the next child's start (child w + 1 of the same parent, on
+    // the next lane), or the parent's end for its last child
+    c.e = cc + 1 == nd.fanout ? nd.e : s_next;
+    c.depth_set = nd.depth_set + 1;  // same set, one level deeper
+    if (c.e > c.s) node_frame(x, c.s, c.e, &c.base, &c.shift);
     nodes[lv1 + w] = c;
     uint64_t* sm = sums + (uint64_t)w * 6;
     for (int t = 0; t < 6; ++t) sm[t] = 0;
   }
 }
 
-// route every point of an internal node to its child; children's rank ranges
-__global__ void level_route(const uint64_t* __restrict__ x, uint64_t S, DNode* nodes, uint32_t* pnode,
-                            const uint32_t* ctrl) {
-  const uint32_t lv0 = ctrl[kLevelNodes + 0], lv1 = ctrl[kLevelNodes + 1];
-  if (lv0 >= lv1) return;
-  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < S; k += (uint64_t)gridDim.x * blockDim.x) {
-    uint32_t v = pnode[k];
-    if (v == kSettled || v < lv0 || v >= lv1) continue;
-    const DNode nd = nodes[v];
-    if (!nd.fanout) {
-      pnode[k] = kSettled;
-      continue;
-    }
-    const uint32_t cds = nd.depth_set + 1;  // same set, one level deeper
-    uint32_t c = route(nd, x[k]);
-    pnode[k] = nd.child0 + c;
-    int pc = (k == nd.s) ? -1 : (int)route(nd, x[k - 1]);
-    for (int cc = pc + 1; cc <= (int)c; ++cc) {
-      nodes[nd.child0 + cc].s = (uint32_t)k;
-      nodes[nd.child0 + cc].depth_set = cds;
-      if (cc >= 1) nodes[nd.child0 + cc - 1].e = (uint32_t)k;
-    }
-    if (k == nd.e - 1) {
-      for (uint32_t cc = c + 1; cc < nd.fanout; ++cc) {
-        nodes[nd.child0 + cc].s = nd.e;
-        nodes[nd.child0 + cc].depth_set = cds;
-        nodes[nd.child0 + cc - 1].e = nd.e;
-      }
-      nodes[nd.child0 + nd.fanout - 1].e = nd.e;
-    }
-  }
-}
-
-__global__ void level_advance(uint32_t* ctrl) {
+__device__ __forceinline__ bool advance_level(uint32_t* ctrl) {
   uint32_t lv1 = ctrl[kLevelNodes + 1];
   ctrl[kLevelNodes + 0] = lv1;
   ctrl[kLevelNodes + 1] = lv1 + ctrl[kLevelNodes + 2];
+  const bool more = ctrl[kLevelNodes + 2] != 0;
   ctrl[kLevelNodes + 2] = 0;
+  ++ctrl[kLevelNodes + 5];
+  return more;
 }
 
-__device__ __forceinline__ double tree_cdf(const DNode* __restrict__ nodes, uint32_t root, uint64_t x) {
-  DNode v = nodes[root];
-  while (v.fanout) v = nodes[v.child0 + route(v, x)];
-  double y = __fma_rn(v.a, __ull2double_rn(local_u(v, x)), v.b);
-  if (y < v.c) return v.c;
-  if (y > v.h) return v.h;
-  return y;
+__global__ void level_advance(uint32_t* ctrl) { advance_level(ctrl); }
+
+// the last kernel of the device loop's body: repeat while the new level has
+// nodes and the depth limit allows another
+__global__ void level_advance_loop(uint32_t* ctrl, cudaGraphConditionalHandle h, uint32_t max_levels) {
+  const bool more = advance_level(ctrl);
+  cudaGraphSetConditional(h, (more && ctrl[kLevelNodes + 5] < max_levels) ? 1u : 0u);
 }
 
-__device__ __forceinline__ uint32_t tree_bin(const DNode* __restrict__ nodes, uint32_t root, uint64_t x,
-                                             uint32_t log2B) {
+// bin of x at leaf v: F clamped to the leaf's rank range, min(B-1, floor(B F))
+__device__ __forceinline__ uint32_t leaf_bin(const DNode& v, uint64_t x, uint32_t log2B) {
   const uint32_t B = 1u << log2B;
-  const uint32_t q = __double2uint_rz(__dmul_rn(tree_cdf(nodes, root, x), __uint2double_rn(B)));
+  double y = __fma_rn(v.a, __ull2double_rn(local_u(v, x)), v.b);
+  if (y < v.c) y = v.c;
+  else if (y > v.h) y = v.h;
+  const uint32_t q = __double2uint_rz(__dmul_rn(y, __uint2double_rn(B)));
   return q < B ? q : B - 1;
 }
 
-// fine-bin splitters: t[q] = smallest encoding whose bin is >= q (t[0] = 0);
-// 95^9 when no key reaches bin q.  The bin is a monotone function of the
-// encoding, so a bisection over any bracket [lo, hi] holding the answer gives
-// the same t[q] as one over the whole range; the bracket comes from the
-// sorted sample xs (the model was fitted to its ranks, so the bin of xs[k] is
-// near B k / S): start at k = q S / B and gallop outwards to a sample key on
-// each side of the answer, then bisect between them.
-__global__ void splitter_kernel(const DNode* __restrict__ nodes, uint32_t log2B, uint64_t* t,
-                                const uint64_t* __restrict__ xs, uint64_t S) {
+// bin at leaf v as a function of the local coordinate u (monotone in u)
+__device__ __forceinline__ uint32_t leaf_bin_u(const DNode& v, uint64_t u, uint32_t log2B) {
   const uint32_t B = 1u << log2B;
-  for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < B; q += gridDim.x * blockDim.x) {
-    if (q == 0) {
-      t[0] = 0;
-      continue;
+  double y = __fma_rn(v.a, __ull2double_rn(u), v.b);
+  if (y < v.c) y = v.c;
+  else if (y > v.h) y = v.h;
+  const uint32_t q = __double2uint_rz(__dmul_rn(y, __uint2double_rn(B)));
+  return q < B ? q : B - 1;
+}
+
+// Smallest x in [lo, hi) whose bin at leaf v is >= q, hi if none; every key
+// of [lo, hi) routes to v.  Keys with the same local coordinate u = (x -
+// base) >> shift share a bin, so the search runs over u: the first u of the
+// range whose bin is >= q, started from the line's inverse (first_at_least),
+// and the key is then the first one with that u.
+__device__ __forceinline__ uint64_t leaf_lower_bound(const DNode& v, uint64_t lo, uint64_t hi, uint32_t q,
+                                                     uint32_t log2B) {
+  if (lo >= hi) return hi;
+  const uint64_t u0 = local_u(v, lo), u1 = local_u(v, hi - 1);
+  if (leaf_bin_u(v, u0, log2B) >= q) return lo;
+  if (leaf_bin_u(v, u1, log2B) < q) return hi;
+  const double g = (v.a > 0.0) ? __ddiv_rn(__dsub_rn(__ddiv_rn(__uint2double_rn(q), __uint2double_rn(1u << log2B)), v.b), v.a)
+                               : -1.0;
+  const uint64_t m = (g > (double)u0 && g < (double)u1) ? (uint64_t)g : ~0ull;
+  const uint64_t ub = first_at_least([&](uint64_t u) { return leaf_bin_u(v, u, log2B); }, u0, u1, q, m);
+  return v.base + (ub << v.shift);  // > lo, as ub > u0
+}
+
+// Smallest x in [lo, hi] whose bin is >= q, given that the answer lies in
+// [lo, hi] (hi itself is never evaluated).  Routers are monotone in x, so
+// when lo and hi take the same child of a node, so does every key between
+// them: the search descends to the deepest node that holds the whole
+// bracket, bisects (full descents from there) while the bracket spans
+// several of its children, and finishes inside one leaf by leaf_lower_bound.
+__device__ __forceinline__ uint64_t bin_lower_bound(const DNode* __restrict__ nodes, uint32_t root, uint64_t lo,
+                                                    uint64_t hi, uint32_t q, uint32_t log2B) {
+  DNode v = nodes[root];
+  while (lo < hi) {
+    while (v.fanout) {
+      const uint32_t c = route(v, lo);
+      if (c != route(v, hi)) break;
+      v = nodes[v.child0 + c];
     }
-    uint64_t lo = 0, hi = kEncTop;  // the answer lies in [lo, hi]
-    if (S) {
-      uint64_t k = ((uint64_t)q * S) >> log2B;  // q < 2^20, S < 2^24: no overflow
-      if (k > S - 1) k = S - 1;
-      if (tree_bin(nodes, 0, xs[k], log2B) >= q) {  // answer <= xs[k]: walk down to a key below it
-        hi = xs[k];
-        for (uint64_t step = 1;; step <<= 1) {
-          if (k == 0) break;  // lo stays 0
-          const uint64_t i = k > step ? k - step : 0;
-          if (tree_bin(nodes, 0, xs[i], log2B) >= q) {
-            hi = xs[i];
-            k = i;
-          } else {
-            lo = xs[i] + 1;
-            break;
-          }
-        }
-      } else {  // answer > xs[k]: walk up to a key at or above it
-        lo = xs[k] + 1;
-        for (uint64_t step = 1;; step <<= 1) {
-          if (k == S - 1) break;  // hi stays 95^9
-          const uint64_t i = k + step < S - 1 ? k + step : S - 1;
-          if (tree_bin(nodes, 0, xs[i], log2B) >= q) {
-            hi = xs[i];
-            break;
-          }
-          lo = xs[i] + 1;
-          k = i;
-        }
-      }
-    }
-    while (lo < hi) {
-      uint64_t mid = lo + ((hi - lo) >> 1);
-      if (tree_bin(nodes, 0, mid, log2B) >= q) hi = mid;
-      else lo = mid + 1;
-    }
-    t[q] = lo;
+    if (!v.fanout) return leaf_lower_bound(v, lo, hi, q, log2B);
+    const uint64_t mid = lo + ((hi - lo) >> 1);
+    DNode w = nodes[v.child0 + route(v, mid)];
+    while (w.fanout) w = nodes[w.child0 + route(w, mid)];
+    if (leaf_bin(w, mid, log2B) >= q) hi = mid;
+    else lo = mid + 1;
+  }
+  return lo;
+}
+
+// bin of every sorted sample point, at the leaf it settled in (set k's
+// points with set k's bin count; lb == nullptr: one set of 2^log2B bins)
+__global__ void point_bins_kernel(const uint64_t* __restrict__ x, uint64_t S, const DNode* __restrict__ nodes,
+                                  const uint32_t* __restrict__ pnode, const SetInfo* __restrict__ sets, uint32_t K,
+                                  const uint32_t* __restrict__ lb, uint32_t log2B, uint32_t* __restrict__ pbin) {
+  for (uint64_t j = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; j < S; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t l = lb ? lb[set_of_point(sets, K, j)] : log2B;
+    pbin[j] = leaf_bin(nodes[pnode[j] & ~kSettledBit], x[j], l);
   }
 }
 
-// the same for K trees: global bin g belongs to set k with tbase[k] <= g < tbase[k+1]
-__global__ void splitter_batch_kernel(const DNode* __restrict__ nodes, uint32_t K, const uint32_t* __restrict__ log2B,
-                                      const uint64_t* __restrict__ tbase, uint64_t total, uint64_t* t) {
-  for (uint64_t g = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; g < total; g += (uint64_t)gridDim.x * blockDim.x) {
+// The sample bracket of bin q in one record set (sorted points xs[0, S),
+// their bins pb and leaves pl): k = the first point whose bin is >= q (S if
+// none), found by a gallop from the guess g (the model was fitted to the
+// ranks, so the bin of xs[k] is near B k / S) and a bisection; the answer
+// lies in [xs[k-1] + 1, xs[k]] (0 and 95^9 past the ends).  Returns the leaf
+// when both ends settled in the same leaf (then every key of the bracket
+// routes there), else kSettled.
+__device__ __forceinline__ uint32_t sample_bracket(uint32_t q, uint64_t g, const uint64_t* __restrict__ xs,
+                                                   const uint32_t* __restrict__ pb, const uint32_t* __restrict__ pl,
+                                                   uint64_t S, uint64_t* lo, uint64_t* hi) {
+  const uint64_t a = gallop_lower_bound(pb, 0, S, q, g);
+  *lo = a ? xs[a - 1] + 1 : 0;
+  *hi = a < S ? xs[a] : kEncTop;
+  return (a && a < S && pl[a - 1] == pl[a]) ? pl[a] & ~kSettledBit : kSettled;
+}
+
+constexpr int kSplitThreads = 256;
+constexpr uint32_t kSplitChunk = kSplitThreads;  // bins per block round
+
+// Fine-bin splitters: t[q] = smallest encoding whose bin is >= q (t[0] = 0;
+// 95^9 when no key reaches bin q).  The bin is a monotone function of the
+// encoding, so any bracket holding the answer gives the same t[q]; the
+// bracket comes from the sorted sample and its bins.  A block takes a chunk
+// of bins: those whose bracket lies in one leaf are inverted there at once
+// (leaf_lower_bound); the rest (about one in T, where a leaf boundary falls
+// between two sample points) are queued in shared memory and searched
+// afterwards by the whole block, so the FP64 descents of bin_lower_bound run
+// in full warps.  Set k (k < K) has its tree at node k, its points at
+// sets[k], its bins at tbase[k] .. tbase[k+1]; K == 1 with tbase == nullptr
+// is one set of 2^log2B bins.
+__global__ void __launch_bounds__(kSplitThreads) splitter_kernel(const DNode* __restrict__ nodes, uint32_t K,
+                                                                const SetInfo* __restrict__ sets,
+                                                                const uint32_t* __restrict__ lb, uint32_t log2B,
+                                                                const uint64_t* __restrict__ tbase, uint64_t total,
+                                                                const uint64_t* __restrict__ xs,
+                                                                const uint32_t* __restrict__ pnode,
+                                                                const uint32_t* __restrict__ pbin, uint64_t* t) {
+  __shared__ uint32_t queue[kSplitChunk];
+  __shared__ uint32_t qn;
+  auto set_of_bin = [&](uint64_t g) -> uint32_t {
+    if (!tbase) return 0;
     uint32_t lo = 0, hi = K - 1;
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
       if (tbase[mid] <= g) lo = mid;
       else hi = mid - 1;
     }
-    const uint32_t k = lo, lb = log2B[k];
-    const uint32_t q = (uint32_t)(g - tbase[k]);
-    if (q == 0) {
-      t[g] = 0;
-      continue;
+    return lo;
+  };
+  for (uint64_t c0 = blockIdx.x * (uint64_t)kSplitChunk; c0 < total; c0 += (uint64_t)gridDim.x * kSplitChunk) {
+    const uint32_t cn = (uint32_t)(total - c0 < kSplitChunk ? total - c0 : kSplitChunk);
+    if (threadIdx.x == 0) qn = 0;
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < cn; i += kSplitThreads) {
+      const uint64_t g = c0 + i;
+      const uint32_t k = set_of_bin(g);
+      const uint32_t q = (uint32_t)(g - (tbase ? tbase[k] : 0));
+      if (q == 0) {
+        t[g] = 0;
+        continue;
+      }
+      const uint64_t so = sets[k].soff, Sk = sets[k].S;
+      const uint32_t l2 = lb ? lb[k] : log2B;
+      uint64_t lo, hi;
+      const uint32_t leaf = sample_bracket(q, ((uint64_t)q * Sk) >> l2, xs + so, pbin + so, pnode + so, Sk, &lo, &hi);
+      if (leaf != kSettled) t[g] = leaf_lower_bound(nodes[leaf], lo, hi, q, l2);
+      else queue[atomicAdd(&qn, 1u)] = i;
     }
-    uint64_t a = 0, b = kEncTop;
-    while (a < b) {
-      const uint64_t mid = a + ((b - a) >> 1);
-      if (tree_bin(nodes, k, mid, lb) >= q) b = mid;
-      else a = mid + 1;
+    __syncthreads();
+    for (uint32_t j = threadIdx.x; j < qn; j += kSplitThreads) {
+      const uint64_t g = c0 + queue[j];
+      const uint32_t k = set_of_bin(g);
+      const uint32_t q = (uint32_t)(g - (tbase ? tbase[k] : 0));
+      const uint64_t so = sets[k].soff, Sk = sets[k].S;
+      const uint32_t l2 = lb ? lb[k] : log2B;
+      uint64_t lo, hi;
+      sample_bracket(q, ((uint64_t)q * Sk) >> l2, xs + so, pbin + so, pnode + so, Sk, &lo, &hi);
+      t[g] = bin_lower_bound(nodes, k, lo, hi, q, l2);
     }
-    t[g] = a;
+    __syncthreads();
   }
 }
+
 
 // radix index of the splitters, level 1: cells c with t[q] <= c << 42 < t[q+1] hold q
 __global__ void fine_lut_kernel(const uint64_t* __restrict__ t, uint32_t log2B, uint4* __restrict__ lut) {
@@ -551,8 +873,10 @@ __device__ __forceinline__ uint32_t block_sum_1024(uint32_t v, uint32_t* wsum) {
   for (int w = 0; w < 32; ++w) t += wsum[w];
   return t;
 }
-__global__ void __launch_bounds__(1024) lut_block_sizes_kernel(const uint4* __restrict__ lut, uint32_t* __restrict__ part) {
+__global__ void __launch_bounds__(1024) lut_block_sizes_kernel(const uint4* __restrict__ lut, uint32_t* __restrict__ part,
+                                                               uint32_t* __restrict__ big) {
   __shared__ uint32_t wsum[32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) big[0] = 0;
   const uint32_t c = blockIdx.x * 1024 + threadIdx.x;
   const uint32_t nb = c < kFineLutCells ? lut_cell_bits(lut, c) : 0;
   const uint32_t t = block_sum_1024(nb ? (1u << nb) + 1 : 0, wsum);
@@ -561,7 +885,8 @@ __global__ void __launch_bounds__(1024) lut_block_sizes_kernel(const uint4* __re
 
 // level-2 offsets: exclusive scan of the sizes (block carry from the block
 // totals before it), written into the cells' .y as (offset << 5) | nb
-__global__ void __launch_bounds__(1024) lut_offsets_kernel(uint4* __restrict__ lut, const uint32_t* __restrict__ part) {
+__global__ void __launch_bounds__(1024) lut_offsets_kernel(uint4* __restrict__ lut, const uint32_t* __restrict__ part,
+                                                           uint32_t* __restrict__ big) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t carry_sh;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -594,28 +919,73 @@ __global__ void __launch_bounds__(1024) lut_offsets_kernel(uint4* __restrict__ l
   // every block reads its cells' .x before any block writes .y: the two are
   // separate words, so the reads of the neighbours' .x stay valid
   if (c < kFineLutCells) lut[c].y = nb ? ((carry_sh + wsum[warp] + incl - v) << 5) | nb : 0u;
+  if (nb > kLutWarpBits) big[1 + atomicAdd(big, 1u)] = c;  // filled by a block
 }
 
-// level-2 entries: a warp per dense cell, lanes over its sub-cell starts;
-// entry k = largest q in the cell's range with t[q] <= the sub-cell's start
+// Level-2 entries [k0, k1) of dense cell c: entry k = the largest q in the
+// cell's range [q0, q1] with t[q] <= the start of sub-cell k.  A bisection
+// for the first, then a walk (entries are non-decreasing in k).
+__device__ __forceinline__ void lut_fill_run(const uint64_t* __restrict__ t, uint32_t q0, uint32_t q1, uint32_t c,
+                                             uint32_t nb, uint32_t k0, uint32_t k1, uint32_t* __restrict__ l2) {
+  const uint64_t start = (uint64_t)c << kFineLutShift;
+  uint64_t v = start + ((uint64_t)k0 << (kFineLutShift - nb));
+  uint32_t lo = q0, hi = q1;  // t[q0] <= v, answer <= q1
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (t[mid] <= v) lo = mid;
+    else hi = mid - 1;
+  }
+  uint64_t next = lo < q1 ? t[lo + 1] : ~0ull;
+  for (uint32_t k = k0;;) {
+    l2[k] = lo;
+    if (++k == k1) break;
+    v = start + ((uint64_t)k << (kFineLutShift - nb));
+    while (next <= v) {  // then lo < q1
+      ++lo;
+      next = lo < q1 ? t[lo + 1] : ~0ull;
+    }
+  }
+}
+
+// level-2 entries of the cells of up to 2^kLutWarpBits sub-cells: a warp per
+// cell, each lane a run of consecutive entries
 __global__ void lut_fill_kernel(const uint64_t* __restrict__ t, const uint4* __restrict__ lut, uint32_t* __restrict__ l2) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (blockDim.x >> 5);
   for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c + 1 < kFineLutCells; c += warps) {
     const uint4 a = lut[c];
-    if (!a.y) continue;
-    const uint32_t nb = a.y & 31, off = a.y >> 5;
+    const uint32_t nb = a.y & 31;
+    if (!a.y || nb > kLutWarpBits) continue;
+    const uint32_t m = (1u << nb) + 1, per = (m + 31) / 32;
+    const uint32_t k0 = lane * per, k1 = min(m, k0 + per);
+    if (k0 < k1) lut_fill_run(t, a.x, lut[c + 1].x, c, nb, k0, k1, l2 + (a.y >> 5));
+  }
+}
+
+// The cells listed in big (more than 2^kLutWarpBits sub-cells, more than 256
+// splitters): a block per cell, its threads over the cell's splitters q0 ..
+// q1 (t[q0] <= the cell's start < t[q0 + 1], t[q1] <= the next cell's start
+// < t[q1 + 1]).  Splitter q owns the entries whose sub-cell start lies in
+// [t[q], t[q + 1]): the first is the start's ceiling in sub-cell units (0
+// for q0), the last ends where q + 1's begin (the table's end for q1).  No
+// dependent loads, so a dense cell costs two loads per splitter.
+__global__ void lut_fill_big_kernel(const uint64_t* __restrict__ t, const uint4* __restrict__ lut,
+                                    const uint32_t* __restrict__ big, uint32_t* __restrict__ l2) {
+  const uint32_t count = big[0];
+  for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+    const uint32_t c = big[1 + i];
+    const uint4 a = lut[c];
+    const uint32_t nb = a.y & 31, m = (1u << nb) + 1, sh = kFineLutShift - nb;
     const uint32_t q0 = a.x, q1 = lut[c + 1].x;
     const uint64_t start = (uint64_t)c << kFineLutShift;
-    for (uint32_t k = lane; k <= (1u << nb); k += 32) {
-      const uint64_t v = start + ((uint64_t)k << (kFineLutShift - nb));
-      uint32_t lo = q0, hi = q1;  // t[q0] <= v, answer <= q1
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi + 1) >> 1;
-        if (t[mid] <= v) lo = mid;
-        else hi = mid - 1;
-      }
-      l2[off + k] = lo;
+    uint32_t* e = l2 + (a.y >> 5);
+    auto first_entry = [&](uint32_t q) -> uint32_t {  // q0 < q <= q1: start < t[q] <= start + 2^42
+      return (uint32_t)((t[q] - start + (1ull << sh) - 1) >> sh);
+    };
+    for (uint32_t q = q0 + threadIdx.x; q <= q1; q += blockDim.x) {
+      const uint32_t k0 = q == q0 ? 0u : first_entry(q);
+      const uint32_t k1 = q == q1 ? m : first_entry(q + 1);
+      for (uint32_t k = k0; k < k1; ++k) e[k] = q;
     }
   }
 }
@@ -634,6 +1004,7 @@ __global__ void set_single_kernel(SetInfo* sets, uint64_t S) {
 
 __global__ void write_header(ModelHeader h, ModelHeader* dst, const uint32_t* ctrl) {
   h.num_nodes = ctrl[kLevelNodes + 3];
+  h.levels = ctrl[kLevelNodes + 5];
   *dst = h;
 }
 
@@ -692,9 +1063,9 @@ cudaError_t fit_radix(const FitArgs& a) {
   const uint32_t B = 1u << a.log2B;
   radix_splitter_kernel<<<(B + 255) / 256, 256, 0, a.stream>>>(a.log2B, t);
   build_fine_lut(t, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut), a.stream);
-  cudaMemsetAsync(a.ctrl + kLevelNodes + 3, 0, 4, a.stream);  // no RMI nodes
+  cudaMemsetAsync(a.ctrl + kLevelNodes + 3, 0, 3 * 4, a.stream);  // no RMI nodes, no levels
   write_header<<<1, 1, 0, a.stream>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
-  *a.launches += 6;
+  *a.launches += 2 + kFineLutLaunches;
   return cudaGetLastError();
 }
 
@@ -711,11 +1082,14 @@ cudaError_t build_fine_lut(const uint64_t* splitters, uint32_t log2B, uint32_t* 
   uint32_t* l2 = lut + kLutL1Words * kFineLutCells;
   fine_lut_kernel<<<(B + 255) / 256, 256, 0, st>>>(splitters, log2B, l1);
   const uint32_t blocks = (kFineLutCells + 1023) / 1024;
-  // block totals go to the last 256 words of level 2, which the entries never reach
+  // block totals go to the last 256 words of level 2 and the list of large
+  // cells before them: the entries never reach either
   uint32_t* part = l2 + lut_level2_words(log2B) - 256;
-  lut_block_sizes_kernel<<<blocks, 1024, 0, st>>>(l1, part);
-  lut_offsets_kernel<<<blocks, 1024, 0, st>>>(l1, part);
+  uint32_t* big = part - lut_big_words(log2B);
+  lut_block_sizes_kernel<<<blocks, 1024, 0, st>>>(l1, part, big);
+  lut_offsets_kernel<<<blocks, 1024, 0, st>>>(l1, part, big);
   lut_fill_kernel<<<(kFineLutCells + 7) / 8, 256, 0, st>>>(splitters, l1, l2);
+  lut_fill_big_kernel<<<(unsigned)sm_count() * 2, 256, 0, st>>>(splitters, l1, big, l2);
   return cudaGetLastError();
 }
 
@@ -730,47 +1104,160 @@ int sm_count() {
   return cached;
 }
 
-cudaError_t build_rmi_levels(const RmiLevelsArgs& a, uint32_t* nodes_out, uint32_t* levels_out) {
+namespace {
+
+// Executable graphs of the device level loop, one per argument set (a graph
+// with a conditional node has one instantiation); kept for reuse, as
+// successive calls on one workspace pass the same pointers.
+struct LevelLoop {
+  int dev;
+  RmiLevelsArgs a;
+  unsigned ngrid, sgrid;
+  cudaGraph_t g;
+  cudaGraphExec_t exec;
+};
+std::mutex g_loop_mu;
+std::vector<LevelLoop> g_loops;
+constexpr size_t kMaxLoops = 32;
+
+bool same_loop(const LevelLoop& l, int dev, const RmiLevelsArgs& a, unsigned ngrid, unsigned sgrid) {
+  return l.dev == dev && l.a.x == a.x && l.a.S_total == a.S_total && l.a.sets == a.sets && l.a.K == a.K &&
+         l.a.T == a.T && l.a.Dmax == a.Dmax && l.a.node_cap == a.node_cap && l.a.nodes == a.nodes &&
+         l.a.pnode == a.pnode && l.a.sums == a.sums && l.a.fc == a.fc && l.a.ctrl == a.ctrl && l.ngrid == ngrid &&
+         l.sgrid == sgrid;
+}
+
+// the loop: a while-node whose body is one level (fit, child numbering,
+// finalisation, the next level's nodes, routing with the children's sums,
+// advance); the handle starts at 1 on every launch and the body's last
+// kernel sets it
+cudaError_t make_level_loop(const RmiLevelsArgs& a, unsigned ngrid, unsigned sgrid, cudaGraph_t* g_out,
+                            cudaGraphExec_t* exec_out) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  cudaGraphConditionalHandle h = 0;
+  if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cond = nullptr;
+  if (e == cudaSuccess) e = cudaGraphAddNode(&cond, g, nullptr, nullptr, 0, &cp);
+  cudaGraph_t body = e == cudaSuccess ? cp.conditional.phGraph_out[0] : nullptr;
+  cudaGraphNode_t prev = nullptr;
+  auto add = [&](const void* fn, unsigned grid, unsigned block, void** args) {
+    if (e != cudaSuccess) return;
+    cudaKernelNodeParams kp = {};
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(block);
+    kp.kernelParams = args;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddKernelNode(&node, body, prev ? &prev : nullptr, prev ? 1 : 0, &kp);
+    prev = node;
+  };
+  const uint64_t* x = a.x;
+  uint64_t S = a.S_total, cap = a.node_cap;
+  DNode* nodes = a.nodes;
+  uint32_t* pnode = a.pnode;
+  uint64_t* sums = a.sums;
+  uint32_t* fc = a.fc;
+  uint32_t* childoff = a.fc + a.node_cap;
+  uint32_t* ctrl = a.ctrl;
+  const SetInfo* sets = a.sets;
+  uint32_t T = a.T, Dmax = a.Dmax, max_levels = a.Dmax + 1;
+  void* fit_args[] = {&x, &nodes, &sums, &fc, &T, &Dmax, &ctrl};
+  add((const void*)level_fit, ngrid, 256, fit_args);
+  void* scan_args[] = {&fc, &childoff, &cap, &ctrl};
+  add((const void*)level_scan, 1, kScanThreads, scan_args);
+  void* fin_args[] = {&nodes, &fc, &childoff, &sets, &ctrl};
+  add((const void*)level_finalize, ngrid, 256, fin_args);
+  void* init_args[] = {&nodes, &sums, &childoff, &x, &ctrl};
+  add((const void*)level_init_next, ngrid, 256, init_args);
+  void* sums_args[] = {&x, &S, &nodes, &pnode, &sums, &ctrl};
+  add((const void*)level_sums<true>, sgrid, 256, sums_args);
+  void* adv_args[] = {&ctrl, &h, &max_levels};
+  add((const void*)level_advance_loop, 1, 1, adv_args);
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+  if (e != cudaSuccess) {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    return e;
+  }
+  *g_out = g;
+  *exec_out = exec;
+  return cudaSuccess;
+}
+
+// launch the device loop for a on its stream (building or reusing its graph)
+cudaError_t launch_level_loop(const RmiLevelsArgs& a, unsigned ngrid, unsigned sgrid) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_loop_mu);
+  for (auto& l : g_loops)
+    if (same_loop(l, dev, a, ngrid, sgrid)) return cudaGraphLaunch(l.exec, a.stream);
+  if (g_loops.size() >= kMaxLoops) {  // retire the oldest, once no launch of it can be in flight
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    for (auto& l : g_loops) {
+      cudaGraphExecDestroy(l.exec);
+      cudaGraphDestroy(l.g);
+    }
+    g_loops.clear();
+  }
+  LevelLoop l = {};
+  l.dev = dev;
+  l.a = a;
+  l.ngrid = ngrid;
+  l.sgrid = sgrid;
+  if ((e = make_level_loop(a, ngrid, sgrid, &l.g, &l.exec)) != cudaSuccess) return e;
+  g_loops.push_back(l);
+  return cudaGraphLaunch(l.exec, a.stream);
+}
+
+}  // namespace
+
+cudaError_t build_rmi_levels(const RmiLevelsArgs& a) {
   cudaStream_t st = a.stream;
   const int sms = sm_count();
   const unsigned pgrid = (unsigned)umin64((a.S_total + 255) / 256 + 1, (uint64_t)sms * 8);
   const unsigned ngrid = (unsigned)sms * 8;
+  const unsigned sgrid = (unsigned)umin64((a.S_total + kSumsBlockPoints - 1) / kSumsBlockPoints + 1, (uint64_t)sms * 8);
   cudaMemsetAsync(a.sums, 0, (size_t)a.K * 6 * sizeof(uint64_t), st);
-  init_roots<<<pgrid, 256, 0, st>>>(a.nodes, a.pnode, a.sets, a.K, a.S_total, a.ctrl);
-  *a.launches += 1;
-  uint32_t host_ctrl[4] = {0, a.K, 0, a.K};
-  uint32_t levels = 0;
+  init_roots<<<pgrid, 256, 0, st>>>(a.x, a.nodes, a.pnode, a.sets, a.K, a.S_total, a.ctrl);
+  level_sums<false><<<sgrid, 256, 0, st>>>(a.x, a.S_total, a.nodes, a.pnode, a.sums, a.ctrl);
+  *a.launches += 2;
+  if (a.device_loop) {
+    *a.launches += 1;  // one graph launch (six kernels per level)
+    return launch_level_loop(a, ngrid, sgrid);
+  }
   const uint32_t max_levels = a.Dmax + 1;
   for (uint32_t lv = 0; lv < max_levels; ++lv) {
-    level_sums<<<pgrid, 256, 0, st>>>(a.x, a.S_total, a.nodes, a.pnode, a.sums, a.ctrl);
     level_fit<<<ngrid, 256, 0, st>>>(a.x, a.nodes, a.sums, a.fc, a.T, a.Dmax, a.ctrl);
     level_scan<<<1, kScanThreads, 0, st>>>(a.fc, a.fc + a.node_cap, a.node_cap, a.ctrl);
     level_finalize<<<ngrid, 256, 0, st>>>(a.nodes, a.fc, a.fc + a.node_cap, a.sets, a.ctrl);
-    level_init_next<<<ngrid, 256, 0, st>>>(a.nodes, a.sums, a.ctrl);
-    level_route<<<pgrid, 256, 0, st>>>(a.x, a.S_total, a.nodes, a.pnode, a.ctrl);
+    level_init_next<<<ngrid, 256, 0, st>>>(a.nodes, a.sums, a.fc + a.node_cap, a.x, a.ctrl);
+    level_sums<true><<<sgrid, 256, 0, st>>>(a.x, a.S_total, a.nodes, a.pnode, a.sums, a.ctrl);
     level_advance<<<1, 1, 0, st>>>(a.ctrl);
-    *a.launches += 7;
-    ++levels;
-    if (a.host_sync) {
-      cudaError_t err = cudaMemcpyAsync(host_ctrl, a.ctrl + kLevelNodes, sizeof(host_ctrl), cudaMemcpyDeviceToHost, st);
-      if (err != cudaSuccess) return err;
-      if ((err = cudaStreamSynchronize(st)) != cudaSuccess) return err;
-      if (host_ctrl[0] == host_ctrl[1]) break;
-    }
+    *a.launches += 6;
   }
-  *nodes_out = host_ctrl[3];
-  *levels_out = levels;
   return cudaGetLastError();
 }
 
-cudaError_t splitters_batch(const DNode* nodes, uint32_t K, const uint32_t* log2B, const uint64_t* tbase,
-                            uint64_t total_bins, uint64_t* t, cudaStream_t st) {
-  const unsigned grid = (unsigned)umin64((total_bins + 127) / 128 + 1, (uint64_t)sm_count() * 16);
-  splitter_batch_kernel<<<grid, 128, 0, st>>>(nodes, K, log2B, tbase, total_bins, t);
+cudaError_t splitters_batch(const DNode* nodes, uint32_t K, const SetInfo* sets, const uint32_t* log2B,
+                            const uint64_t* tbase, uint64_t total_bins, const uint64_t* x, uint64_t S_total,
+                            const uint32_t* pnode, uint32_t* pbin, uint64_t* t, cudaStream_t st) {
+  const unsigned pgrid = (unsigned)umin64((S_total + 255) / 256 + 1, (uint64_t)sm_count() * 8);
+  point_bins_kernel<<<pgrid, 256, 0, st>>>(x, S_total, nodes, pnode, sets, K, log2B, 0, pbin);
+  const unsigned grid = (unsigned)umin64((total_bins + kSplitChunk - 1) / kSplitChunk, (uint64_t)sm_count() * 16);
+  splitter_kernel<<<grid ? grid : 1, kSplitThreads, 0, st>>>(nodes, K, sets, log2B, 0, tbase, total_bins, x, pnode,
+                                                             pbin, t);
   return cudaGetLastError();
 }
 
-cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sorted_out) {
+cudaError_t fit_rmi(const FitArgs& a, const uint64_t** sorted_out) {
   const uint64_t S = a.S;
   const uint64_t cap = node_cap_for(S, a.T);
   uint8_t* mb = static_cast<uint8_t*>(a.model);
@@ -828,20 +1315,21 @@ cudaError_t fit_rmi(const FitArgs& a, uint32_t* nodes_out, const uint64_t** sort
   la.sums = a.sums;
   la.fc = a.fc;
   la.ctrl = a.ctrl;
-  la.host_sync = true;
+  la.device_loop = true;
   la.stream = st;
   la.launches = a.launches;
-  uint32_t nodes_total = 0, levels = 0;
-  cudaError_t err = build_rmi_levels(la, &nodes_total, &levels);
+  cudaError_t err = build_rmi_levels(la);
   if (err != cudaSuccess) return err;
-  h.levels = levels;
-  // 4. splitters of the fine bins
+  // 4. splitters of the fine bins (the bins of the sample points in the sums' place)
   const uint32_t B = 1u << a.log2B;
-  splitter_kernel<<<(B + 127) / 128, 128, 0, st>>>(nodes, a.log2B, splitters, x, S);
+  uint32_t* pbin = reinterpret_cast<uint32_t*>(a.sums);
+  const unsigned pgrid = (unsigned)umin64((S + 255) / 256 + 1, (uint64_t)sms * 8);
+  point_bins_kernel<<<pgrid, 256, 0, st>>>(x, S, nodes, a.pnode, a.sets, 1, nullptr, a.log2B, pbin);
+  splitter_kernel<<<(B + kSplitChunk - 1) / kSplitChunk, kSplitThreads, 0, st>>>(nodes, 1, a.sets, nullptr, a.log2B,
+                                                                                nullptr, B, x, a.pnode, pbin, splitters);
   build_fine_lut(splitters, a.log2B, reinterpret_cast<uint32_t*>(mb + ml.lut), st);
   write_header<<<1, 1, 0, st>>>(h, reinterpret_cast<ModelHeader*>(mb), a.ctrl);
-  L += 3;
-  *nodes_out = nodes_total;
+  L += 3 + kFineLutLaunches;
   return cudaGetLastError();
 }
 

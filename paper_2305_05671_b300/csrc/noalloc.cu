@@ -62,5 +62,6 @@ extern "C" elsar_status elsar_sort_noalloc(const void* d_in, void* d_out, uint64
     scratch = g_scratch_ptr[dev];
   }
   // elsar_sort clears, on the stream, every scratch word that must start at zero
-  return elsar_sort(d_in, d_out, n, p, scratch, ELSAR_NOALLOC_SCRATCH_BYTES, stream, nullptr);
+  const elsar_status s = elsar_sort(d_in, d_out, n, p, scratch, ELSAR_NOALLOC_SCRATCH_BYTES, stream, nullptr);
+  return (s == ELSAR_OK && n) ? elsar_wait(scratch, ELSAR_NOALLOC_SCRATCH_BYTES, stream) : s;
 }

@@ -60,6 +60,14 @@ def test_sizes_and_buffers_rejected_on_host():
     assert L.elsar_sort(None, None, 0, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 0
 
 
+def test_wait_arguments_rejected_on_host():
+    L = elsar.lib()
+    assert L.elsar_wait(None, 1 << 20, None) == 1  # no workspace
+    assert L.elsar_wait(FAKE_WS + 16, 1 << 20, None) == 1  # not 256-byte aligned
+    assert L.elsar_wait(FAKE_WS, 64, None) == 1  # smaller than the control words
+    assert L.elsar_last_error()
+
+
 def test_status_strings():
     L = elsar.lib()
     for s in range(7):

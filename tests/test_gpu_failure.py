@@ -43,8 +43,9 @@ def test_production_waits_run_out_and_the_next_sort_is_exact(in_off):
     plain-load classify, and the coarse scatter's batch waits give up.  The
     CTA raises the status word, drains its own copies and returns; every later
     kernel reads the word and does nothing, so the sort kernel writes no record;
-    the call returns ELSAR_ETIMEOUT, and the next call on the same workspace
-    sorts exactly."""
+    the call returns ELSAR_ETIMEOUT (with stats; without, the next elsar_wait
+    on the workspace does), and the next call on the same workspace sorts
+    exactly."""
     n = 200_000
     host = recgen.generate_cpu(n, recgen.KeySpec("zipf", s=1.1, dup=0.05, seed=14))
     big = torch.zeros(n * 100 + 16, dtype=torch.uint8, device="cuda")
@@ -53,9 +54,16 @@ def test_production_waits_run_out_and_the_next_sort_is_exact(in_off):
     d_out = torch.full((n * 100,), 0xEE, dtype=torch.uint8, device="cuda")
     p = elsar.Params(num_partitions=64, seed=3, wait_limit_cycles=1)
     ws = elsar.alloc_workspace(n, p)
+    # with stats the call waits and reports its own timeout
     with pytest.raises(elsar.ElsarError) as e:
-        elsar.sort(d_in, d_out, n, p, ws=ws)
+        elsar.sort(d_in, d_out, n, p, ws=ws, stats=True)
     assert e.value.status == 4  # ELSAR_ETIMEOUT
+    # without stats it returns at once; elsar_wait reports the timeout, once
+    elsar.sort(d_in, d_out, n, p, ws=ws)
+    with pytest.raises(elsar.ElsarError) as e:
+        elsar.wait(ws)
+    assert e.value.status == 4
+    elsar.wait(ws)
     torch.cuda.synchronize()
     out = d_out.cpu().numpy().reshape(n, 100)
     if in_off == 0:
@@ -64,5 +72,30 @@ def test_production_waits_run_out_and_the_next_sort_is_exact(in_off):
     assert not np.array_equal(d_out.cpu().numpy(), oracle.stable_sort(host))
     p.wait_limit_cycles = 0
     elsar.sort(d_in, d_out, n, p, ws=ws)
-    torch.cuda.synchronize()
+    elsar.wait(ws)
     assert np.array_equal(d_out.cpu().numpy(), oracle.stable_sort(host))
+
+
+def test_asynchronous_sorts_on_a_stream_then_wait():
+    """Without stats elsar_sort only enqueues its work (the RMI's levels run
+    in a device-side loop): two sorts on a side stream, each with its own
+    workspace, are exact once elsar_wait has synchronised the stream; a
+    workspace no call has used reports no timeout."""
+    n = 120_000
+    hosts = [recgen.generate_cpu(n, spec) for spec in (recgen.KeySpec("uniform", seed=21),
+                                                       recgen.KeySpec("zipf", s=1.3, dup=0.1, seed=22))]
+    p = elsar.Params(num_partitions=64, seed=5)
+    fresh = elsar.alloc_workspace(n, p)
+    fresh.fill_(0x5A)  # whatever a new allocation holds
+    elsar.wait(fresh)
+    side = torch.cuda.Stream()
+    ins = [torch.from_numpy(h).cuda() for h in hosts]
+    outs = [torch.empty_like(d) for d in ins]
+    wss = [elsar.alloc_workspace(n, p) for _ in ins]
+    torch.cuda.synchronize()
+    for d, o, w in zip(ins, outs, wss):
+        elsar.sort(d, o, n, p, ws=w, stream=side.cuda_stream)
+    for w in wss:
+        elsar.wait(w, stream=side.cuda_stream)
+    for h, o in zip(hosts, outs):
+        assert np.array_equal(o.cpu().numpy(), oracle.stable_sort(h))
