@@ -10,6 +10,8 @@ namespace {
 
 inline uint64_t umin64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 inline uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+// log2 of a power of two
+inline uint32_t ilog2(uint64_t v) { return 63 - __builtin_clzll(v); }
 
 constexpr int kThreads = 256;
 constexpr int kUnroll = 8;
@@ -404,11 +406,19 @@ __device__ __forceinline__ uint32_t upper_set(const uint64_t* __restrict__ off, 
 // shared counter, offsets from a block scan), then written out slot by slot,
 // so the pairs of one bin leave as one contiguous run (whole lines rather
 // than 16-byte pieces scattered over the device).  cur[] holds every bin's
-// next output slot and advances by the batch's counts.  Waits on the copies
-// are bounded like classify's.
+// next output slot.  Four block barriers per batch: the counts are complete
+// (the input buffer is free again), two in the scan, the offsets are set,
+// the batch is placed; the owner of a bin turns its offset into the bin's
+// output base (base = cur - off), advances cur and clears the count while
+// setting the offset, so no barrier follows the write-out.  Waits on the
+// copies are bounded like classify's.
 constexpr int kStageThreads = 512;
 constexpr int kStagePer = 4;
 constexpr uint32_t kStagePairs = kStageThreads * kStagePer;  // 2048 pairs = 32 KB
+// the classify units the coarse pass takes are powers of two that divide a batch
+static_assert((kTileRecs & (kTileRecs - 1)) == 0 && kStagePairs % kTileRecs == 0, "classify tile");
+static_assert(((kThreads * kUnroll) & (kThreads * kUnroll - 1)) == 0 && kStagePairs % (kThreads * kUnroll) == 0,
+              "plain classify unit");
 
 struct Stage {
   Pair* in[2];      // kStagePairs each: input batches (bulk-copy targets)
@@ -416,11 +426,14 @@ struct Stage {
   uint16_t* binof;  // kStagePairs
   uint32_t* cnt;    // nb: counts of the batch
   uint32_t* off;    // nb: exclusive offsets in the batch
+  uint32_t* base;   // nb: output slot of the batch's slot 0 of each bin (cur - off)
   uint32_t* cur;    // nb: next output slot
-  uint32_t* wsum;   // 33
+  uint32_t* wsum;   // 33: the scan's warp sums, then [32] = the batch's pair count
   uint64_t* bar;    // 2
 };
 
+// block-wide exclusive scan of one value per thread (two barriers; wsum is
+// next written by the following batch's scan, after its own barriers)
 __device__ __forceinline__ uint32_t stage_scan(uint32_t v, uint32_t* wsum) {
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t incl = v;
@@ -440,29 +453,36 @@ __device__ __forceinline__ uint32_t stage_scan(uint32_t v, uint32_t* wsum) {
     if (lane < kStageThreads / 32) wsum[lane] = wi - w;
   }
   __syncthreads();
-  const uint32_t r = wsum[warp] + incl - v;
-  __syncthreads();
-  return r;
+  return wsum[warp] + incl - v;
 }
 
-// one batch: p[k] valid when bin[k] < nb; out slots checked against `bound`
-__device__ void stage_scatter(const Stage& S, uint32_t nb, const Pair (&p)[kStagePer], const uint32_t (&bin)[kStagePer],
-                              Pair* __restrict__ out, uint64_t bound) {
-  uint32_t r[kStagePer];
+// rank of the batch's pairs inside their bins (p[k] valid when bin[k] < nb);
+// before the barrier that ends the count
+__device__ __forceinline__ void stage_count(const Stage& S, uint32_t nb, const uint32_t (&bin)[kStagePer],
+                                            uint32_t (&r)[kStagePer]) {
 #pragma unroll
   for (int k = 0; k < kStagePer; ++k)
     if (bin[k] < nb) r[k] = atomicAdd(&S.cnt[bin[k]], 1u);
-  __syncthreads();
-  // exclusive offsets of the nb counts: each thread scans a contiguous group
+}
+
+// the rest of a counted batch; out slots checked against `bound`
+__device__ void stage_scatter(const Stage& S, uint32_t nb, const Pair (&p)[kStagePer], const uint32_t (&bin)[kStagePer],
+                              const uint32_t (&r)[kStagePer], Pair* __restrict__ out, uint64_t bound) {
+  // exclusive offsets of the nb counts: each thread owns a contiguous group of bins
   const uint32_t per = (nb + kStageThreads - 1) / kStageThreads;
   const uint32_t g0 = min(nb, threadIdx.x * per), g1 = min(nb, g0 + per);
   uint32_t local = 0;
   for (uint32_t c = g0; c < g1; ++c) local += S.cnt[c];
   uint32_t run = stage_scan(local, S.wsum);
   for (uint32_t c = g0; c < g1; ++c) {
+    const uint32_t k = S.cnt[c];
     S.off[c] = run;
-    run += S.cnt[c];
+    S.base[c] = S.cur[c] - run;
+    S.cur[c] += k;
+    S.cnt[c] = 0;
+    run += k;
   }
+  if (g1 == nb && g0 < g1) S.wsum[32] = run;  // the batch's pair count
   __syncthreads();
 #pragma unroll
   for (int k = 0; k < kStagePer; ++k)
@@ -472,18 +492,11 @@ __device__ void stage_scatter(const Stage& S, uint32_t nb, const Pair (&p)[kStag
       S.binof[sl] = (uint16_t)bin[k];
     }
   __syncthreads();
-  const uint32_t total = S.off[nb - 1] + S.cnt[nb - 1];
+  const uint32_t total = S.wsum[32];
   for (uint32_t sl = threadIdx.x; sl < total; sl += kStageThreads) {
-    const uint32_t c = S.binof[sl];
-    const uint64_t dst = (uint64_t)S.cur[c] + (sl - S.off[c]);
+    const uint64_t dst = (uint64_t)S.base[S.binof[sl]] + sl;
     if (dst < bound) out[dst] = S.pairs[sl];
   }
-  __syncthreads();
-  for (uint32_t c = threadIdx.x; c < nb; c += kStageThreads) {
-    S.cur[c] += S.cnt[c];
-    S.cnt[c] = 0;
-  }
-  __syncthreads();
 }
 
 __device__ __forceinline__ Stage carve_stage(uint8_t* smem, uint32_t nb) {
@@ -495,14 +508,15 @@ __device__ __forceinline__ Stage carve_stage(uint8_t* smem, uint32_t nb) {
   uint32_t* w = reinterpret_cast<uint32_t*>(S.binof + kStagePairs);
   S.cnt = w;
   S.off = w + nb;
-  S.cur = w + 2 * nb;
-  S.wsum = w + 3 * nb;
-  S.bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(w + 3 * nb + 33 + 1) & ~(uintptr_t)7);
+  S.base = w + 2 * nb;
+  S.cur = w + 3 * nb;
+  S.wsum = w + 4 * nb;
+  S.bar = reinterpret_cast<uint64_t*>(reinterpret_cast<uintptr_t>(w + 4 * nb + 33 + 1) & ~(uintptr_t)7);
   return S;
 }
 
 size_t stage_smem_bytes(uint32_t nb) {
-  return (size_t)kStagePairs * (3 * sizeof(Pair) + 2) + (3 * (size_t)nb + 33 + 1) * 4 + 2 * 8 + 8;
+  return (size_t)kStagePairs * (3 * sizeof(Pair) + 2) + (4 * (size_t)nb + 33 + 1) * 4 + 2 * 8 + 8;
 }
 
 // Pass B1: pairs (input order) -> coarse-bin order.  With K record sets
@@ -515,7 +529,7 @@ size_t stage_smem_bytes(uint32_t nb) {
 // the fine bin in lo; the fine bin's place inside its coarse bin rides in
 // bits 48.. of lo for pass B2.
 __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const Pair* __restrict__ in, uint64_t n,
-                                                                       uint32_t U, int tail_to_first,
+                                                                       uint32_t log2U, int tail_to_first,
                                                                        const uint32_t* __restrict__ seg,
                                                                        uint32_t seg_stride, uint32_t cshift,
                                                                        uint32_t C, Pair* __restrict__ out,
@@ -535,22 +549,24 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
   }
   __syncthreads();
   const uint32_t fmask = (1u << cshift) - 1;
+  const uint32_t U = 1u << log2U, umask = U - 1;
   const uint64_t G = gridDim.x, b = blockIdx.x;
-  const uint64_t nfull = n / U;
+  const uint64_t nfull = n >> log2U;
+  const uint32_t rag = (uint32_t)(n & umask);
   const uint64_t mine_full = b < nfull ? (nfull - b + G - 1) / G : 0;
-  const bool tail = (n % U) && b == (tail_to_first ? 0 : nfull % G);
+  const bool tail = rag && b == (tail_to_first ? 0 : nfull % G);
   const uint64_t mine = mine_full + (tail ? 1 : 0);  // units of this CTA: b, b+G, ..., then the ragged one
-  const uint32_t upb = kStagePairs / U;                // units per batch (U divides kStagePairs)
+  const uint32_t upb = kStagePairs >> log2U;           // units per batch (U divides kStagePairs)
   const uint64_t nbatch = (mine + upb - 1) / upb;
   // unit k of this CTA: its first record and its size
   auto unit_of = [&](uint64_t k, uint64_t* first) -> uint32_t {
     if (k < mine_full) {
-      *first = (b + k * G) * U;
+      *first = (b + k * G) << log2U;
       return U;
     }
     if (k < mine) {
-      *first = nfull * U;
-      return (uint32_t)(n % U);
+      *first = nfull << log2U;
+      return rag;
     }
     *first = 0;
     return 0;
@@ -586,19 +602,21 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
     for (int k = 0; k < kStagePer; ++k) {
       const uint32_t slot = threadIdx.x + k * kStageThreads;
       uint64_t first;
-      const uint32_t c = unit_of(j * upb + slot / U, &first);
+      const uint32_t c = unit_of(j * upb + (slot >> log2U), &first);
       bin[k] = ~0u;
-      if (ok && slot % U < c) {
+      if (ok && (slot & umask) < c) {
         const Pair q = S.in[buf][slot];
         const uint32_t f = (uint32_t)q.lo;
         bin[k] = min(f >> cshift, C - 1);
         p[k].hi = q.hi;
-        const uint64_t g = first + slot % U;  // the record's place in the input (all sets together)
+        const uint64_t g = first + (slot & umask);  // the record's place in the input (all sets together)
         const uint64_t i = poff ? g - poff[upper_set(poff, K, g)] : g;
         p[k].lo = (q.lo & 0x0000FFFF00000000ull) | ((uint64_t)(f & fmask) << 48) | (uint32_t)i;
       }
     }
-    if (__syncthreads_or(!ok)) {  // every thread is also done reading input buffer `buf`
+    uint32_t r[kStagePer];
+    stage_count(S, C, bin, r);
+    if (__syncthreads_or(!ok)) {  // the counts are complete, and input buffer `buf` is read
       if (threadIdx.x == 0) {
         atomicOr(ctrl + kStatusWord, 1u);
         for (int q = 0; q < 2; ++q)  // copies in flight target this CTA's shared memory: wait, bounded
@@ -611,7 +629,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) coarse_scatter_kernel(const 
       issue(j + 2, buf);
       ++issued[buf];
     }
-    stage_scatter(S, C, p, bin, out, n);
+    stage_scatter(S, C, p, bin, r, out, n);
   }
 }
 
@@ -668,7 +686,9 @@ __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pa
         p[k].lo = q.lo & 0x0000FFFFFFFFFFFFull;
       }
     }
-    if (__syncthreads_or(!ok)) {
+    uint32_t r[kStagePer];
+    stage_count(S, nf, bin, r);
+    if (__syncthreads_or(!ok)) {  // the counts are complete, and input buffer `buf` is read
       if (threadIdx.x == 0) {
         atomicOr(ctrl + kStatusWord, 1u);
         for (int q = 0; q < 2; ++q)
@@ -681,7 +701,7 @@ __global__ void __launch_bounds__(kStageThreads, 2) fine_scatter_kernel(const Pa
       issue(j + 2, buf);
       ++issued[buf];
     }
-    stage_scatter(S, nf, p, bin, out, e);
+    stage_scatter(S, nf, p, bin, r, out, e);
   }
 }
 
@@ -796,7 +816,7 @@ cudaError_t partition_batch(const BatchPartArgs& a) {
                                                a.cursor, cshift, a.seg_hist, (uint32_t)segs);
   scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
   coarse_offsets_kernel<<<(C + 7) / 8, 256, 0, st>>>(a.seg_hist, (uint32_t)segs, G, C, cshift, a.bin_off, a.ctrl);
-  coarse_scatter_kernel<<<G, kStageThreads, stage_smem_bytes(C), st>>>(a.pairs, a.N, kThreads, 0, a.seg_hist,
+  coarse_scatter_kernel<<<G, kStageThreads, stage_smem_bytes(C), st>>>(a.pairs, a.N, ilog2(kThreads), 0, a.seg_hist,
                                                                         (uint32_t)segs, cshift, C, a.pairs_in_order,
                                                                         a.ctrl, a.poff, a.K, kWaitLimitCycles);
   fine_scatter_kernel<<<C, kStageThreads, stage_smem_bytes(1u << cshift), st>>>(a.pairs_in_order, a.bin_off, a.B,
@@ -862,7 +882,7 @@ cudaError_t partition_records(const PartArgs& a) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);
   if (cs == cudaStreamCaptureStatusNone) prepare_scatter_kernels();
-  coarse_scatter_kernel<<<G, kStageThreads, smem1, st>>>(pin, a.n, U, tail_to_first, a.seg_hist, seg_stride, cshift,
+  coarse_scatter_kernel<<<G, kStageThreads, smem1, st>>>(pin, a.n, ilog2(U), tail_to_first, a.seg_hist, seg_stride, cshift,
                                                           C, static_cast<Pair*>(a.mid), a.ctrl, nullptr, 0,
                                                           a.wait_limit);
   fine_scatter_kernel<<<C, kStageThreads, smem2, st>>>(static_cast<const Pair*>(a.mid), a.bin_off, B, cshift,
