@@ -215,63 +215,77 @@ __global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __res
 
 constexpr int kScanThreads = 1024;
 
-// block-wide exclusive scan of one value per thread; returns the total
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* excl, uint32_t* wsum) {
-  uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  uint32_t incl = v;
+constexpr int kTileChunks = 16;  // 32-element chunks per warp and tile of the single-CTA scans
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+  const uint32_t lane = threadIdx.x & 31;
   for (int d = 1; d < 32; d <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, incl, d);
-    if (lane >= (uint32_t)d) incl += y;
+    const uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+    if (lane >= (uint32_t)d) v += y;
   }
-  if (lane == 31) wsum[warp] = incl;
+  return v;
+}
+
+// exclusive scan of the warps' totals: wsum[w] in, wsum[w] = the warps
+// before w out, wsum[32] = the tile's total (two barriers)
+__device__ __forceinline__ void scan_warp_totals(uint32_t* wsum) {
   __syncthreads();
-  if (warp == 0) {
-    uint32_t nw = blockDim.x >> 5;
-    uint32_t w = lane < nw ? wsum[lane] : 0;
-    uint32_t wi = w;
-    for (int d = 1; d < 32; d <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, wi, d);
-      if (lane >= (uint32_t)d) wi += y;
-    }
+  const uint32_t lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    const uint32_t nw = blockDim.x >> 5;
+    const uint32_t w = lane < nw ? wsum[lane] : 0;
+    const uint32_t wi = warp_incl_scan(w);
     if (lane < nw) wsum[lane] = wi - w;
     if (lane == 31) wsum[32] = wi;
   }
   __syncthreads();
-  *excl = wsum[warp] + incl - v;
-  uint32_t total = wsum[32];
-  __syncthreads();
-  return total;
 }
 
 // Single CTA: bin offsets (exclusive scan of the histogram), scatter cursors,
-// max bin.  Coalesced tiles of kScanThreads bins with a running carry.
+// max bin.  A tile is kScanThreads x kTileChunks bins; warp w scans chunks of
+// 32 consecutive bins (coalesced) across its part, then the warps' totals
+// are scanned and a running carry joins the tiles.  Each bin is read and
+// written by one thread (hist and cursor may be the same array).
 __global__ void __launch_bounds__(kScanThreads) scan_bins(const uint32_t* hist, uint32_t B,
                                                           uint32_t* __restrict__ bin_off, uint32_t* cursor,
                                                           uint32_t* ctrl) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t carry_sh;
   if (ctrl[kStatusWord]) return;  // classify gave up: nothing downstream runs
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry_sh = 0;
   uint32_t mx = 0;
   __syncthreads();
-  for (uint32_t base = 0; base < B; base += kScanThreads) {
-    const uint32_t q = base + threadIdx.x;
-    const uint32_t h = q < B ? hist[q] : 0;  // hist and cursor may be the same array
-    mx = max(mx, h);
-    uint32_t excl;
-    const uint32_t tot = block_exclusive_scan(h, &excl, wsum);
-    const uint32_t carry = carry_sh;
-    if (q < B) {
-      bin_off[q] = carry + excl;
-      cursor[q] = carry + excl;
+  for (uint32_t base = 0; base < B; base += kScanThreads * kTileChunks) {
+    const uint32_t w0 = base + warp * 32 * kTileChunks;
+    uint32_t ex[kTileChunks], run = 0;
+#pragma unroll
+    for (int j = 0; j < kTileChunks; ++j) {
+      const uint32_t q = w0 + j * 32 + lane;
+      const uint32_t h = q < B ? hist[q] : 0;
+      mx = max(mx, h);
+      const uint32_t incl = warp_incl_scan(h);
+      ex[j] = run + incl - h;
+      run += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) wsum[warp] = run;
+    scan_warp_totals(wsum);
+    const uint32_t off = carry_sh + wsum[warp];
+#pragma unroll
+    for (int j = 0; j < kTileChunks; ++j) {
+      const uint32_t q = w0 + j * 32 + lane;
+      if (q < B) {
+        bin_off[q] = off + ex[j];
+        cursor[q] = off + ex[j];
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 0) carry_sh = carry + tot;
+    if (threadIdx.x == 0) carry_sh += wsum[32];
     __syncthreads();
   }
   if (threadIdx.x == 0) bin_off[B] = carry_sh;
   for (int d = 16; d; d >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
-  if ((threadIdx.x & 31) == 0) atomicMax(ctrl + kMaxBin, mx);
+  if (lane == 0) atomicMax(ctrl + kMaxBin, mx);
 }
 
 // Partition cuts.  Paper rule: c_p = p * B / P.  Refined rule: the boundary t
@@ -323,7 +337,8 @@ __global__ void cuts_kernel(const uint32_t* __restrict__ bin_off, uint32_t log2B
 // bin that is not small, or its start offset enters a new W-window; a run of
 // small bins inside one window holds < 2W = cap pairs.  Oversize bins
 // (> cap pairs) are listed separately.  item_flag becomes the item id of
-// every bin.  Coalesced tiles with a running carry.
+// every bin.  Tiles of kScanThreads x kTileChunks bins as in scan_bins, each
+// bin read and written by one thread.
 __global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __restrict__ bin_off, uint32_t B,
                                                              uint32_t cap, uint32_t* item_flag, uint32_t* items,
                                                              uint32_t* oversize, uint32_t* ctrl) {
@@ -331,33 +346,48 @@ __global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __r
   __shared__ uint32_t carry_sh;
   if (ctrl[kStatusWord]) return;
   const uint32_t W = cap / 2;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry_sh = 0;
   __syncthreads();
-  for (uint32_t base = 0; base < B; base += kScanThreads) {
-    const uint32_t q = base + threadIdx.x;
-    uint32_t f = 0;
-    if (q < B) {
-      const uint32_t o = bin_off[q], cnt = bin_off[q + 1] - o;
-      f = item_flag[q] != 0 || q == 0 || cnt > W;
-      if (!f) {
-        const uint32_t po = bin_off[q - 1];
-        f = (o - po) > W || (o / W) != (po / W);
+  for (uint32_t base = 0; base < B; base += kScanThreads * kTileChunks) {
+    const uint32_t w0 = base + warp * 32 * kTileChunks;
+    uint32_t ex[kTileChunks], run = 0, fl = 0;  // fl bit j: bin of chunk j starts an item
+#pragma unroll
+    for (int j = 0; j < kTileChunks; ++j) {
+      const uint32_t q = w0 + j * 32 + lane;
+      uint32_t f = 0;
+      if (q < B) {
+        const uint32_t o = bin_off[q], cnt = bin_off[q + 1] - o;
+        f = item_flag[q] != 0 || q == 0 || cnt > W;
+        if (!f) {
+          const uint32_t po = bin_off[q - 1];
+          f = (o - po) > W || (o / W) != (po / W);
+        }
       }
+      fl |= f << j;
+      const uint32_t incl = warp_incl_scan(f);
+      ex[j] = run + incl - f;
+      run += __shfl_sync(0xffffffffu, incl, 31);
     }
-    uint32_t excl;
-    const uint32_t tot = block_exclusive_scan(f, &excl, wsum);
-    const uint32_t id = carry_sh + excl;
-    if (q < B) {
-      if (f) {
-        items[id] = q;
-        if (bin_off[q + 1] - bin_off[q] > cap) oversize[atomicAdd(ctrl + kNumOversize, 1u)] = id;
-        item_flag[q] = id;
-      } else {
-        item_flag[q] = id - 1;
+    if (lane == 0) wsum[warp] = run;
+    scan_warp_totals(wsum);
+    const uint32_t off = carry_sh + wsum[warp];
+#pragma unroll
+    for (int j = 0; j < kTileChunks; ++j) {
+      const uint32_t q = w0 + j * 32 + lane;
+      if (q < B) {
+        const uint32_t id = off + ex[j];
+        if ((fl >> j) & 1) {
+          items[id] = q;
+          if (bin_off[q + 1] - bin_off[q] > cap) oversize[atomicAdd(ctrl + kNumOversize, 1u)] = id;
+          item_flag[q] = id;
+        } else {
+          item_flag[q] = id - 1;
+        }
       }
     }
     __syncthreads();
-    if (threadIdx.x == 0) carry_sh += tot;
+    if (threadIdx.x == 0) carry_sh += wsum[32];
     __syncthreads();
   }
   if (threadIdx.x == 0) {
