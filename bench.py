@@ -272,30 +272,46 @@ def run_elsar(args):
         d = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
         recgen.generate_gpu(d, n, wl["spec"], stream=stream.cuda_stream)
         ins.append(d)
-    out = torch.empty(n * RECORD, dtype=torch.uint8, device=dev)
-    ws = elsar.alloc_workspace(n, p, device=dev)
+    # K streams, each with its own workspace and output: set i sorts on stream i mod K (K = 1: one
+    # after the other on one stream)
+    K = max(1, min(args.streams, len(ins)))
+    streams = [stream] + [torch.cuda.Stream(dev) for _ in range(K - 1)]
+    outs = [torch.empty(n * RECORD, dtype=torch.uint8, device=dev) for _ in range(K)]
+    wss = [elsar.alloc_workspace(n, p, device=dev) for _ in range(K)]
+    out, ws = outs[0], wss[0]
     torch.cuda.synchronize()
 
     def step(params, stats=False):
         # without stats each sort only enqueues its work (no host round trip); elsar_wait after the
         # timed region reports any device-side timeout of the step's sorts
-        sts = [elsar.sort(d, out, n, params, ws=ws, stream=stream, stats=stats) for d in ins]
+        sts = [elsar.sort(d, outs[i % K], n, params, ws=wss[i % K], stream=streams[i % K], stats=stats)
+               for i, d in enumerate(ins)]
         return sts
+
+    def wait_all():
+        for w, s in zip(wss, streams):
+            elsar.wait(w, s)
 
     for _ in range(args.warmup):
         step(p)
-    elsar.wait(ws, stream)
+    wait_all()
     torch.cuda.synchronize()
     barrier(world)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
         ev0.record(stream)
+        for s in streams[1:]:
+            s.wait_event(ev0)
         for _ in range(args.steps):
             step(p)
+        for s in streams[1:]:
+            e = torch.cuda.Event()
+            e.record(s)
+            stream.wait_event(e)
         ev1.record(stream)
         torch.cuda.synchronize()
-    elsar.wait(ws, stream)
+    wait_all()
     barrier(world)
     ms = ev0.elapsed_time(ev1) / args.steps
     ms = max_over_ranks(ms, world)
@@ -328,11 +344,17 @@ def run_elsar(args):
     torch.cuda.synchronize()
     if not args.no_plain:
         ev0.record(stream)
+        for s in streams[1:]:
+            s.wait_event(ev0)
         for _ in range(args.steps):
             step(p_plain, stats=False)
+        for s in streams[1:]:
+            e = torch.cuda.Event()
+            e.record(s)
+            stream.wait_event(e)
         ev1.record(stream)
         torch.cuda.synchronize()
-        elsar.wait(ws, stream)
+        wait_all()
         plain_ms = ev0.elapsed_time(ev1) / args.steps
         plain = {"value": round(bytes_per_step / (plain_ms / 1e3) / 1e9, 2), "ms_per_step": round(plain_ms, 3),
                  "form": "paper partition rule, one sort launch per partition"}
@@ -359,10 +381,10 @@ def run_elsar(args):
                "steps": args.e2e_steps}
         del d_in
     if not args.no_ooc:
-        del ws, out
+        del ws, out, wss, outs
         torch.cuda.empty_cache()
         ooc = run_ooc(args, h_ins, h_out, n, dev, stream)
-    ins = out = ws = None  # the step's device buffers are not needed any more
+    ins = out = ws = wss = outs = None  # the step's device buffers are not needed any more
     torch.cuda.empty_cache()
     batched = None if args.no_batched else run_batched(args, dev, stream)
     cfg4 = None if args.no_cfg4 else run_cfg4(args, dev, stream)
@@ -375,7 +397,7 @@ def run_elsar(args):
         "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic", "config": workload_config({"tile_pairs": args.tile_pairs or 2048, "n_records_per_set": n,
-                                   "sets": len(workloads())}),
+                                   "sets": len(workloads()), "streams": K}),
         "records_per_s": round(world * len(workloads()) * n / (ms / 1e3)),
         "hbm_frac_200B": round(world * len(workloads()) * n * 200 / (ms / 1e3) / 1e9 / peaks["hbm_gbs"], 4),
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "plain": plain, "batched": batched,
@@ -565,6 +587,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="elsar", choices=["elsar", "reference"])
     ap.add_argument("--tile-pairs", type=int, default=0)
+    ap.add_argument("--streams", type=int, default=2, help="sort the step's sets on this many streams at once")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
