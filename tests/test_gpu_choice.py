@@ -7,9 +7,10 @@
 * The choice between the network and the RMI: for the weights the GPU trained,
   the oracle's decision (boundary check, held-out judge, full-data imbalance)
   and its judge counts equal the GPU's, on workloads that reach each outcome:
-  kept, reason 2 (product-Zipf keys), reason 3 (the paper's cut rule at 4096
-  partitions, which no model keeps within 1.1 of the mean on 2M records), and
-  a sample whose smallest key holds half the records.
+  kept, reason 1 (a set whose smallest key holds half the records: F at the
+  first knot is about 1/4), reason 2 (product-Zipf keys), reason 3 (the
+  paper's cut rule at 4096 partitions, which no model keeps within 1.1 of the
+  mean on 2M records).
 * One Adam step of the trainer equals the oracle's step within FP32 rounding.
 """
 import numpy as np
@@ -83,7 +84,8 @@ CASES = {
     "uniform": (lambda: recgen.generate_cpu(1_000_000, recgen.KeySpec("uniform", seed=41)), 256, 50_000, 1, 0, None),
     "zipf11": (lambda: recgen.generate_cpu(1_000_000, recgen.KeySpec("zipf", s=1.1, dup=0.05, seed=42)), 256, 50_000,
                1, 0, 2),
-    "min_heavy": (lambda: _min_heavy(500_000), 256, 20_000, 1, 0, None),
+    # half the sample is the smallest key: the first six knots coincide and F there is about 1/4
+    "min_heavy": (lambda: _min_heavy(500_000), 256, 20_000, 1, 0, 1),
     "paper_rule_4096": (lambda: recgen.generate_cpu(2_000_000, recgen.KeySpec("uniform", seed=43)), 4096, 20_000, 0,
                         elsar.SKIP_JUDGE, 3),
 }
