@@ -185,6 +185,10 @@ elsar_status elsar_sort_partitions(const void* d_records, uint64_t n, const elsa
  * up (ELSAR_ETIMEOUT) is then kept in the workspace and reported by
  * elsar_wait.  With stats, or with model_kind MLP (its checks read counts
  * back), it synchronises `stream` and reports ELSAR_ETIMEOUT itself.
+ * Without stats (RMI or RADIX) the call can be captured into a caller's CUDA
+ * graph, after one call outside any capture (that call sets the kernels'
+ * shared-memory limits); inside a capture the RMI's levels are launched as a
+ * fixed sequence (empty levels exit at once) instead of the device loop.
  * Errors: as the three calls.
  */
 elsar_status elsar_sort(const void* d_in, void* d_out, uint64_t n, const elsar_params* p, void* d_ws,

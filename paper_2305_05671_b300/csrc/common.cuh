@@ -273,9 +273,9 @@ struct FitArgs {
 // Level-by-level RMI construction over K trees at once (K record sets whose
 // sorted samples are concatenated; sets[k] gives each segment).  `device_loop`
 // runs the levels in a graph whose while-node repeats them until a level has
-// no children (single-set path; no host round trip); otherwise a fixed number
-// of levels is launched and empty levels exit at once (capturable in a
-// caller's graph).  The level count ends in ctrl[kLevelNodes + 5], the node
+// no children (single-set path; no host round trip) unless the stream is
+// being captured; otherwise a fixed number of levels is launched and empty
+// levels exit at once (capturable in a caller's graph).  The level count ends in ctrl[kLevelNodes + 5], the node
 // count in ctrl[kLevelNodes + 3].
 struct RmiLevelsArgs {
   const uint64_t* x;  // concatenated sorted samples

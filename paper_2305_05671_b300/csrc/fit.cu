@@ -1229,10 +1229,13 @@ cudaError_t build_rmi_levels(const RmiLevelsArgs& a) {
   init_roots<<<pgrid, 256, 0, st>>>(a.x, a.nodes, a.pnode, a.sets, a.K, a.S_total, a.ctrl);
   level_sums<false><<<sgrid, 256, 0, st>>>(a.x, a.S_total, a.nodes, a.pnode, a.sums, a.ctrl);
   *a.launches += 2;
-  if (a.device_loop) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (a.device_loop && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
     *a.launches += 1;  // one graph launch (six kernels per level)
     return launch_level_loop(a, ngrid, sgrid);
   }
+  // a fixed number of levels (inside a caller's stream capture too, where a
+  // graph with a while-node cannot be embedded); empty levels exit at once
   const uint32_t max_levels = a.Dmax + 1;
   for (uint32_t lv = 0; lv < max_levels; ++lv) {
     level_fit<<<ngrid, 256, 0, st>>>(a.x, a.nodes, a.sums, a.fc, a.T, a.Dmax, a.ctrl);
