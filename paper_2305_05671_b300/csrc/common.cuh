@@ -125,8 +125,9 @@ __device__ __forceinline__ Pair load_pair(const uint8_t* rec, uint32_t idx, cons
 // Level 1 (uint4 per cell): .x = q, the largest index with t[q] <= c <<
 // kFineLutShift; .z/.w = the low and high words of t[q + 1] (95^9 past the
 // last splitter), so a cell holding one splitter is resolved by its own
-// entry; .y = 0, or, for a cell holding more than kLutDense splitters,
-// (offset << 5) | nb: the cell is split into 2^nb sub-cells whose level-2
+// entry; .y = (the cell's splitter count << 5) for a cell of up to kLutDense
+// splitters, or, for a cell holding more, (offset << 5) | nb (nb > 0): the
+// cell is split into 2^nb sub-cells whose level-2
 // entries lut2[offset + k] (k = 0..2^nb) hold the largest q with t[q] <= the
 // sub-cell's start.  Either way the answer for x lies in [lo, hi] of x's cell
 // or sub-cell, and a short binary search finishes it.  The level-2 table
@@ -160,17 +161,20 @@ __device__ __forceinline__ void lut_range(const uint32_t* __restrict__ lut, uint
   const uint32_t c = (uint32_t)(x >> kFineLutShift);
   const uint4 a = __ldg(l1 + c);
   lo = a.x;
-  hi = __ldg(lut + kLutL1Words * (c + 1));  // the next cell's .x
-  if (a.y) {
-    const uint32_t nb = a.y & 31, off = a.y >> 5;
+  const uint32_t nb = a.y & 31;
+  if (nb) {
+    const uint32_t off = a.y >> 5;
     const uint32_t k = (uint32_t)(x >> (kFineLutShift - nb)) & ((1u << nb) - 1);
     const uint32_t* l2 = lut + kLutL1Words * kFineLutCells + off;
     lo = __ldg(l2 + k);
     hi = __ldg(l2 + k + 1);
-  } else if (hi == lo + 1) {  // one splitter in the cell: its value is in the entry
-    const uint64_t next = ((uint64_t)a.w << 32) | a.z;
-    lo = next <= x ? hi : lo;
-    hi = lo;
+  } else {
+    hi = lo + (a.y >> 5);  // the cell's splitter count is in the entry
+    if (hi == lo + 1) {    // one splitter in the cell: its value is in the entry
+      const uint64_t next = ((uint64_t)a.w << 32) | a.z;
+      lo = next <= x ? hi : lo;
+      hi = lo;
+    }
   }
 }
 

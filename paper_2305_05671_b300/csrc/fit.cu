@@ -918,7 +918,9 @@ __global__ void __launch_bounds__(1024) lut_offsets_kernel(uint4* __restrict__ l
   __syncthreads();
   // every block reads its cells' .x before any block writes .y: the two are
   // separate words, so the reads of the neighbours' .x stay valid
-  if (c < kFineLutCells) lut[c].y = nb ? ((carry_sh + wsum[warp] + incl - v) << 5) | nb : 0u;
+  // (a cell of few splitters keeps its count instead, sparing a lookup the next cell's entry)
+  if (c < kFineLutCells)
+    lut[c].y = nb ? ((carry_sh + wsum[warp] + incl - v) << 5) | nb : (c + 1 < kFineLutCells ? lut[c + 1].x - lut[c].x : 0u) << 5;
   if (nb > kLutWarpBits) big[1 + atomicAdd(big, 1u)] = c;  // filled by a block
 }
 
@@ -955,7 +957,7 @@ __global__ void lut_fill_kernel(const uint64_t* __restrict__ t, const uint4* __r
   for (uint32_t c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c + 1 < kFineLutCells; c += warps) {
     const uint4 a = lut[c];
     const uint32_t nb = a.y & 31;
-    if (!a.y || nb > kLutWarpBits) continue;
+    if (!nb || nb > kLutWarpBits) continue;
     const uint32_t m = (1u << nb) + 1, per = (m + 31) / 32;
     const uint32_t k0 = lane * per, k1 = min(m, k0 + per);
     if (k0 < k1) lut_fill_run(t, a.x, lut[c + 1].x, c, nb, k0, k1, l2 + (a.y >> 5));
