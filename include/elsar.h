@@ -204,6 +204,20 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
                              void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
 
 /*
+ * elsar_sort_host without waiting: the copy in, the sort (asynchronous, as
+ * elsar_sort without stats; model_kind MLP waits for its checks) and the
+ * copy out are enqueued on `stream` and the call returns.  With pinned host
+ * buffers the copies are DMA transfers, so sets sorted on different streams
+ * overlap one set's copy out with another's copy in (the host link carries
+ * both directions at once).  The host and device buffers must stay valid
+ * until the stream reaches the end of the call; elsar_wait(d_ws) then waits
+ * for it and reports a device-side timeout.  No paper counterpart.
+ * Errors: EINVAL (null host buffers), and as elsar_sort.
+ */
+elsar_status elsar_sort_host_async(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_in,
+                                   void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream);
+
+/*
  * Status of the asynchronous calls on workspace d_ws (ws_bytes >= 140, the
  * control words that open every workspace): synchronises `stream`, then
  * returns ELSAR_ETIMEOUT if a device-side bounded wait gave up in any

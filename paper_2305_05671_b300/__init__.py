@@ -102,6 +102,7 @@ def lib():
             "elsar_sort": (ctypes.c_int, [P, P, U64, PP, P, SZ, P, ctypes.POINTER(_Stats)]),
             "elsar_sort_host": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
             "elsar_wait": (ctypes.c_int, [P, SZ, P]),
+            "elsar_sort_host_async": (ctypes.c_int, [P, P, U64, PP, P, P, P, SZ, P]),
             "elsar_sort_noalloc": (ctypes.c_int, [P, P, U64, PP, P]),
             "elsar_ooc_min_workspace": (SZ, [U64, PP]),
             "elsar_selftest_bounded_wait": (ctypes.c_int, [P, P, U64, P, ctypes.POINTER(ctypes.c_uint32 * 3)]),
@@ -233,6 +234,12 @@ def sort_host(h_in, h_out, n: int, p: Params, d_in, d_out, ws, stream=None):
     """Host records in (pinned for async DMA), host records out; synchronises."""
     _check(lib().elsar_sort_host(_ptr(h_in), _ptr(h_out), n, ctypes.byref(p.c()), _ptr(d_in), _ptr(d_out), _ptr(ws),
                                  _nbytes(ws), _stream(stream)))
+
+
+def sort_host_async(h_in, h_out, n: int, p: Params, d_in, d_out, ws, stream=None):
+    """sort_host without waiting: copy in, sort and copy out enqueued on `stream`; wait(ws) waits and reports."""
+    _check(lib().elsar_sort_host_async(_ptr(h_in), _ptr(h_out), n, ctypes.byref(p.c()), _ptr(d_in), _ptr(d_out),
+                                       _ptr(ws), _nbytes(ws), _stream(stream)))
 
 
 def ooc_min_workspace(n: int, p: Params | None = None) -> int:

@@ -622,6 +622,21 @@ elsar_status elsar_sort_host(const void* h_in, void* h_out, uint64_t n, const el
   return n ? elsar_wait(d_ws, ws_bytes, stream) : ELSAR_OK;  // synchronises
 }
 
+elsar_status elsar_sort_host_async(const void* h_in, void* h_out, uint64_t n, const elsar_params* p, void* d_in,
+                                   void* d_out, void* d_ws, size_t ws_bytes, elsar_stream_t stream) {
+  g_err.clear();
+  if (n && (!h_in || !h_out)) return fail(ELSAR_EINVAL, "null host buffer");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = n * ELSAR_RECORD_BYTES;
+  cudaError_t e = n ? cudaMemcpyAsync(d_in, h_in, bytes, cudaMemcpyHostToDevice, st) : cudaSuccess;
+  if (e != cudaSuccess) return cuda_fail(e, "copy in");
+  elsar_status s = elsar_sort(d_in, d_out, n, p, d_ws, ws_bytes, stream, nullptr);
+  if (s != ELSAR_OK) return s;
+  if (n && (e = cudaMemcpyAsync(h_out, d_out, bytes, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+    return cuda_fail(e, "copy out");
+  return ELSAR_OK;
+}
+
 elsar_status elsar_wait(void* d_ws, size_t ws_bytes, elsar_stream_t stream) {
   g_err.clear();
   if (!d_ws || !aligned(d_ws, 256) || ws_bytes < (kStickyStatus + 1) * 4)

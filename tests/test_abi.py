@@ -60,6 +60,13 @@ def test_sizes_and_buffers_rejected_on_host():
     assert L.elsar_sort(None, None, 0, ctypes.byref(p), FAKE_WS, 1 << 40, None, None) == 0
 
 
+def test_host_async_arguments_rejected_on_host():
+    L = elsar.lib()
+    p = elsar.Params().c()
+    assert L.elsar_sort_host_async(None, None, 1000, ctypes.byref(p), FAKE_WS, FAKE_WS, FAKE_WS, 1 << 40, None) == 1
+    assert L.elsar_sort_host_async(None, None, 0, ctypes.byref(p), FAKE_WS, FAKE_WS, FAKE_WS, 1 << 40, None) == 0
+
+
 def test_wait_arguments_rejected_on_host():
     L = elsar.lib()
     assert L.elsar_wait(None, 1 << 20, None) == 1  # no workspace

@@ -99,3 +99,26 @@ def test_asynchronous_sorts_on_a_stream_then_wait():
         elsar.wait(w, stream=side.cuda_stream)
     for h, o in zip(hosts, outs):
         assert np.array_equal(o.cpu().numpy(), oracle.stable_sort(h))
+
+
+def test_asynchronous_host_sorts_on_two_streams():
+    """elsar_sort_host_async: pinned host records in and out on two streams
+    (one set's copy back overlapping the other's copy in); after elsar_wait
+    both host outputs equal the oracle's sort."""
+    n = 150_000
+    hosts = [recgen.generate_cpu(n, spec) for spec in (recgen.KeySpec("zipf", s=1.1, dup=0.05, seed=71),
+                                                       recgen.KeySpec("uniform", seed=72))]
+    p = elsar.Params(num_partitions=64, seed=6)
+    h_ins = [torch.from_numpy(h).pin_memory() for h in hosts]
+    h_outs = [torch.empty(n * 100, dtype=torch.uint8).pin_memory() for _ in hosts]
+    d_ins = [torch.empty(n * 100, dtype=torch.uint8, device="cuda") for _ in hosts]
+    d_outs = [torch.empty(n * 100, dtype=torch.uint8, device="cuda") for _ in hosts]
+    wss = [elsar.alloc_workspace(n, p) for _ in hosts]
+    streams = [torch.cuda.Stream() for _ in hosts]
+    torch.cuda.synchronize()
+    for i in range(2):
+        elsar.sort_host_async(h_ins[i], h_outs[i], n, p, d_ins[i], d_outs[i], wss[i], stream=streams[i].cuda_stream)
+    for w, s in zip(wss, streams):
+        elsar.wait(w, stream=s.cuda_stream)
+    for h, o in zip(hosts, h_outs):
+        assert np.array_equal(o.numpy(), oracle.stable_sort(h))
