@@ -122,3 +122,22 @@ def test_asynchronous_host_sorts_on_two_streams():
         elsar.wait(w, stream=s.cuda_stream)
     for h, o in zip(hosts, h_outs):
         assert np.array_equal(o.numpy(), oracle.stable_sort(h))
+
+
+def test_many_workspaces_outgrow_the_level_loop_cache():
+    """The RMI's device loop is a graph instantiated per workspace and kept
+    for reuse (at most 32 at a time; the set is retired after a device
+    synchronisation when it is full): 40 workspaces in turn, each sort exact,
+    then the first workspace again."""
+    n = 20_000
+    host = recgen.generate_cpu(n, recgen.KeySpec("zipf", s=1.3, dup=0.1, seed=81))
+    want = oracle.stable_sort(host)
+    d_in = torch.from_numpy(host).cuda()
+    d_out = torch.empty_like(d_in)
+    p = elsar.Params(num_partitions=16, seed=4)
+    wss = [elsar.alloc_workspace(n, p) for _ in range(40)]
+    for w in wss + wss[:1]:
+        d_out.fill_(0)
+        elsar.sort(d_in, d_out, n, p, ws=w)
+        elsar.wait(w)
+        assert np.array_equal(d_out.cpu().numpy(), want)
