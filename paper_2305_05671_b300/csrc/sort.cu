@@ -37,14 +37,15 @@ constexpr int kWarps = kThreads / 32;
 #define ELSAR_GATHER_WARPS 5
 #endif
 constexpr int kGatherWarps = ELSAR_GATHER_WARPS;  // gatherer warps (after the sorters)
-constexpr int kBlockThreads = kThreads + 32 * kGatherWarps;
+constexpr int kHandThreads = kThreads + 32 * kGatherWarps;  // the sorters and the gatherers
+constexpr int kBlockThreads = kHandThreads + 32;           // and the producer warp (last)
 constexpr uint32_t kSlots = 2;      // hand-over ring between the sorters and the gatherers
 constexpr uint32_t kRankMax = 128;  // buckets up to this length are ranked inside the digit pass (the touch-up)
 
 // named barriers: 1 = the sorter group; FULL[b] = 2 + b and EMPTY[b] = 2 + kSlots + b over the
-// whole CTA (immediate ids, so that the kernel reserves only the barriers it uses)
+// sorters and the gatherers (immediate ids, so that the kernel reserves only the barriers it uses)
 __device__ __forceinline__ void sorter_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kThreads) : "memory"); }
-#define ELSAR_BAR(op, id) asm volatile("bar." op " " #id ", %0;" ::"n"(kBlockThreads) : "memory")
+#define ELSAR_BAR(op, id) asm volatile("bar." op " " #id ", %0;" ::"n"(kHandThreads) : "memory")
 __device__ __forceinline__ void full_arrive(uint32_t b) {
   if (b == 0) ELSAR_BAR("arrive", 2);
   else if (b == 1) ELSAR_BAR("arrive", 3);
@@ -77,8 +78,22 @@ struct Handoff {
   uint32_t mode;          // 0: record indices in the slot's index list, 1: gsorted, 2: no more items
 };
 
+// The next work item, found by the producer warp: its id, first pair, pairs
+// and record set, or the end of the work.
+struct Meta {
+  uint64_t o0;
+  uint32_t it, m, set;
+  uint32_t kind;  // 0: an item to sort, 1: no more items
+};
+constexpr uint32_t kMetaSlots = 2;
+
 struct Misc {
   Handoff ho[kSlots];
+  Meta meta[kMetaSlots];
+  uint64_t meta_full[kMetaSlots];   // the producer posted meta[b] (one arrival)
+  uint64_t meta_empty[kMetaSlots];  // the sorters are done with the item of meta[b] (one arrival)
+  uint32_t meta_ok;                 // sorter thread 0's wait for the next meta succeeded
+  volatile uint32_t heartbeat;      // advanced by the sorters inside long (oversize) items
   uint64_t red[2][kWarps];
   uint64_t kmin, kmax;
   uint32_t nlong, next_long, nsplit;
@@ -528,6 +543,7 @@ __device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0,
     load_tile(t, src + o0 + c0, mc);
     tile_sort(t, mc);
     for (uint32_t j = threadIdx.x; j < mc; j += kThreads) src[o0 + c0 + j] = t.A[t.perm[j]];
+    if (threadIdx.x == 0) ms.heartbeat = ms.heartbeat + 1;  // progress, for the producer's bounded wait
     sorter_sync();
   }
   Pair* A = t.A;
@@ -539,6 +555,7 @@ __device__ const Pair* sort_oversize(const KArgs& k, const Tile& t, uint64_t o0,
       const Pair* ga = src + o0 + p0;
       const Pair* gb = src + o0 + a1;
       if (threadIdx.x < 2) ms.split[threadIdx.x] = merge_split(ga, a1 - p0, gb, b1 - a1, (threadIdx.x ? t1 : t0) - p0);
+      if (threadIdx.x == 0) ms.heartbeat = ms.heartbeat + 1;
       sorter_sync();
       const uint32_t ka0 = (uint32_t)ms.split[0], ka1 = (uint32_t)ms.split[1];
       const uint32_t kb0 = (t0 - p0) - ka0, kb1 = (t1 - p0) - ka1;
@@ -582,27 +599,19 @@ __device__ __forceinline__ uint32_t set_of_bin(const uint64_t* __restrict__ tbas
   return lo;
 }
 
-// Sorter side of one work item: sort it and hand it to the gatherers in slot
-// (slot mod kSlots).  Returns false for an empty item (nothing handed over).
-__device__ bool sort_item(const KArgs& k, const Tile& t, uint32_t it, uint32_t num_items, uint32_t slot) {
-  const uint64_t o0 = k.bin_off[k.items[it]];
-  const uint32_t m = k.bin_off[k.items[it + 1]] - (uint32_t)o0;
-  if (m == 0) return false;
+// Sorter side of one work item (found by the producer): sort it and hand it
+// to the gatherers in slot (slot mod kSlots).
+__device__ void sort_item(const KArgs& k, const Tile& t, const Meta& me, uint32_t slot) {
+  const uint64_t o0 = me.o0;
+  const uint32_t m = me.m;
   // records of this item: one set's buffers (batched path) or the only set
   const uint8_t* in = k.in;
   uint8_t* out = k.out;
   uint64_t base = 0;
   if (k.ins) {
-    const uint32_t s = set_of_bin(k.tbase, k.K, k.items[it]);
-    in = k.ins[s];
-    out = k.outs[s];
-    base = k.poff[s];
-  }
-  if (threadIdx.x == 0 && it + gridDim.x < num_items) {
-    // the pairs of the item this CTA will most likely take next: into L2 now
-    const uint32_t nx = it + gridDim.x;
-    const uint64_t a = k.bin_off[k.items[nx]], b = k.bin_off[k.items[nx + 1]];
-    for (uint64_t q = a * sizeof(Pair); q < b * sizeof(Pair); q += 128) prefetch_l2(reinterpret_cast<const uint8_t*>(k.pairs) + q);
+    in = k.ins[me.set];
+    out = k.outs[me.set];
+    base = k.poff[me.set];
   }
   const uint32_t b = slot % kSlots;
   Handoff h;
@@ -627,7 +636,6 @@ __device__ bool sort_item(const KArgs& k, const Tile& t, uint32_t it, uint32_t n
   if (threadIdx.x == 0) t.ms->ho[b] = h;
   __threadfence_block();  // global (oversize) and shared writes before the hand-over
   full_arrive(b);
-  return true;
 }
 
 // Sorter side: no more items.  Slot n (the number handed over) says so; then
@@ -691,38 +699,124 @@ __device__ __forceinline__ Tile carve(uint8_t* smem, uint32_t cap) {
   return t;
 }
 
+// Bounded wait of the producer for the sorters to finish an item: the clock
+// restarts whenever the sorters advance the heartbeat, so a long oversize
+// item does not run it out while a stall still ends it.
+__device__ bool producer_wait(Misc& ms, uint64_t* bar, uint32_t parity) {
+  long long t0 = clock64();
+  uint32_t hb = ms.heartbeat;
+  while (!mbar_test_wait(bar, parity)) {
+    const uint32_t now = ms.heartbeat;
+    if (now != hb) {
+      hb = now;
+      t0 = clock64();
+    } else if (clock64() - t0 > kWaitLimitCycles) {
+      return false;
+    }
+  }
+  return true;
+}
+
+// Producer warp: finds the CTA's next work item (claimed from the global
+// queue, or the next of its partition), reads where its pairs lie and asks
+// L2 for them, one item ahead of the sorters, so that the claim and the
+// dependent index loads leave the sorters' path.  Item n goes through
+// meta[n mod 2]: meta_full[b] completes when it is posted, meta_empty[b] when
+// the sorters have finished it.
+__device__ void producer_loop(const KArgs& k, Misc& ms) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t num_items = k.ctrl[kNumItems];
+  const uint32_t num_over = k.persistent ? k.ctrl[kNumOversize] : 0;
+  uint32_t next = k.persistent ? 0 : k.part_items[k.part] + blockIdx.x;  // per-partition: the next item id
+  const uint32_t last = k.persistent ? 0 : k.part_items[k.part + 1];
+  for (uint32_t n = 0;; ++n) {
+    const uint32_t b = n % kMetaSlots;
+    uint32_t ok = 1;
+    if (lane == 0 && n >= kMetaSlots) ok = producer_wait(ms, &ms.meta_empty[b], ((n - kMetaSlots) / kMetaSlots) & 1);
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {  // the sorters stopped advancing: report it and stop (their own wait for meta gives up too)
+      if (lane == 0) atomicOr(k.ctrl + kStatusWord, 1u);
+      return;
+    }
+    Meta me = {};
+    me.kind = 1;
+    if (lane == 0) {
+      for (;;) {
+        uint32_t it;
+        if (k.persistent) {
+          const uint32_t j = atomicAdd(k.ctrl + kQueueHead, 1u);
+          if (j >= num_over + num_items) break;
+          it = j < num_over ? k.oversize[j] : j - num_over;
+          const uint64_t a = k.bin_off[k.items[it]], e = k.bin_off[k.items[it + 1]];
+          if (j >= num_over && e - a > k.cap) continue;  // done in the oversize phase
+          if (e == a) continue;
+          me.o0 = a;
+          me.m = (uint32_t)(e - a);
+        } else {
+          if (next >= last) break;
+          it = next;
+          next += gridDim.x;
+          const uint64_t a = k.bin_off[k.items[it]], e = k.bin_off[k.items[it + 1]];
+          if (e == a) continue;
+          me.o0 = a;
+          me.m = (uint32_t)(e - a);
+        }
+        me.it = it;
+        me.set = k.ins ? set_of_bin(k.tbase, k.K, k.items[it]) : 0;
+        me.kind = 0;
+        // the item's pairs into L2 now (16-byte aligned, whole pairs)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(k.pairs + me.o0),
+                     "r"(min(me.m, k.cap) * (uint32_t)sizeof(Pair))
+                     : "memory");
+        break;
+      }
+      ms.meta[b] = me;
+      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&ms.meta_full[b]))
+                   : "memory");
+    }
+    if (__shfl_sync(0xffffffffu, me.kind, 0) == 1) return;
+  }
+}
+
 __global__ void __launch_bounds__(kBlockThreads, 2) sort_gather_kernel(KArgs k) {
   extern __shared__ __align__(16) uint8_t smem[];
   if (k.ctrl[kStatusWord]) return;  // partitioning gave up: no item is valid (uniform over the CTA)
   const Tile t = carve(smem, k.cap);
+  Misc& ms = *t.ms;
+  if (threadIdx.x == 0) {
+    for (uint32_t b = 0; b < kMetaSlots; ++b) {
+      mbar_init(&ms.meta_full[b], 1);
+      mbar_init(&ms.meta_empty[b], 1);
+    }
+    ms.heartbeat = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x >= kHandThreads) {
+    producer_loop(k, ms);
+    return;
+  }
   if (threadIdx.x >= kThreads) {
     gatherer_loop(t);
     return;
   }
-  Misc& ms = *t.ms;
-  const uint32_t num_items = k.ctrl[kNumItems];
   uint32_t slot = 0;
-  if (k.persistent) {
-    const uint32_t num_over = k.ctrl[kNumOversize];
-    for (;;) {
-      if (threadIdx.x == 0) ms.item = atomicAdd(k.ctrl + kQueueHead, 1u);
-      sorter_sync();
-      const uint32_t j = ms.item;
-      sorter_sync();
-      if (j >= num_over + num_items) break;
-      uint32_t it;
-      if (j < num_over) {
-        it = k.oversize[j];
-      } else {
-        it = j - num_over;
-        if (k.bin_off[k.items[it + 1]] - k.bin_off[k.items[it]] > k.cap) continue;  // done in the oversize phase
-      }
-      if (sort_item(k, t, it, num_items, slot)) ++slot;
+  for (uint32_t n = 0;; ++n) {
+    const uint32_t b = n % kMetaSlots;
+    if (threadIdx.x == 0) ms.meta_ok = mbar_wait(&ms.meta_full[b], (n / kMetaSlots) & 1, kWaitLimitCycles) ? 1u : 0u;
+    sorter_sync();
+    if (!ms.meta_ok) {  // the producer stopped: the status word says why (or is set here)
+      if (threadIdx.x == 0) atomicOr(k.ctrl + kStatusWord, 1u);
+      break;
     }
-  } else {
-    const uint32_t i0 = k.part_items[k.part], i1 = k.part_items[k.part + 1];
-    for (uint32_t it = i0 + blockIdx.x; it < i1; it += gridDim.x)
-      if (sort_item(k, t, it, 0, slot)) ++slot;
+    const Meta me = ms.meta[b];
+    if (me.kind == 1) break;
+    sort_item(k, t, me, slot);
+    ++slot;
+    sorter_sync();  // every sorter thread is done with the item (and with meta[b])
+    if (threadIdx.x == 0)
+      asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&ms.meta_empty[b]))
+                   : "memory");
   }
   sorters_done(t, slot);
 }
