@@ -383,34 +383,30 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
     }
   }
   sorter_sync();
-  for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
-    const uint32_t pos = atomicAdd(t.cnt + (uint32_t)((sel_key(t, j, sel) - kmin) >> shift), 1u);
-    t.perm[pos] = (uint16_t)j;
-  }
-  sorter_sync();
   if (ms.nsplit * 8 >= m) {
-    // second counting pass: an element of a bucket [rs, rs + len) of kSplitMin or
-    // more goes to slot rs + sub, sub the next lb = floor(log2 len) bits of its key
-    // below the bucket's digit (2^lb <= len, so the slots stay inside the bucket);
-    // an element of a smaller bucket goes to slot rs.  Slots of different buckets
-    // never mix, so one plain exclusive scan over the tile gives every slot its
-    // final start, and a bucket's slots start at rs.
-    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
-      const uint64_t key = sel_key(t, t.perm[pos], sel);
+    // second counting pass, straight from the first pass's bucket starts (no
+    // placement by the first digit): an element of a bucket [rs, rs + len) of
+    // kSplitMin or more goes to slot rs + sub, sub the next lb = floor(log2 len)
+    // bits of its key below the bucket's digit (2^lb <= len, so the slots stay
+    // inside the bucket); an element of a smaller bucket goes to slot rs.  Slots
+    // of different buckets never mix, so one plain exclusive scan over the tile
+    // gives every slot its final start, and a bucket's slots start at rs.
+    for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
+      const uint64_t key = sel_key(t, j, sel);
       const uint32_t d = (uint32_t)((key - kmin) >> shift);
-      const uint32_t rs = d ? t.cnt[d - 1] : 0, len = t.cnt[d] - rs;
+      const uint32_t rs = t.cnt[d], len = (d + 1 < D ? t.cnt[d + 1] : m) - rs;
       uint32_t x = rs;
       if (len >= kSplitMin) {
         const uint32_t lb = 31 - __clz(len);
         const uint64_t local = (key - kmin) - ((uint64_t)d << shift);
         x = rs + (uint32_t)(shift >= lb ? local >> (shift - lb) : local);
       }
-      t.dig2[pos] = (uint16_t)x;
+      t.dig2[j] = (uint16_t)x;
     }
     sorter_sync();
     for (uint32_t x = threadIdx.x; x < m; x += kThreads) t.cnt[x] = 0;
     sorter_sync();
-    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) atomicAdd(t.cnt + t.dig2[pos], 1u);
+    for (uint32_t j = threadIdx.x; j < m; j += kThreads) atomicAdd(t.cnt + t.dig2[j], 1u);
     sorter_sync();
     {
       const uint32_t per = (m + kThreads - 1) / kThreads;
@@ -425,14 +421,12 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
       }
     }
     sorter_sync();
-    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
-      const uint32_t x = t.dig2[pos];
+    for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
+      const uint32_t x = t.dig2[j];
       const uint32_t np = atomicAdd(t.cnt + x, 1u);
-      t.perm2[np] = t.perm[pos];
+      t.perm[np] = (uint16_t)j;
       t.sb[np] = (uint16_t)x;
     }
-    sorter_sync();
-    for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) t.perm[pos] = t.perm2[pos];
     sorter_sync();
     // slot x now holds [cnt[x-1], cnt[x]); rank inside slots of up to kRankMax
     for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
@@ -447,6 +441,11 @@ __device__ void tile_sort(const Tile& t, uint32_t m) {
     }
     sorter_sync();
   } else {
+    for (uint32_t j = threadIdx.x; j < m; j += kThreads) {
+      const uint32_t pos = atomicAdd(t.cnt + (uint32_t)((sel_key(t, j, sel) - kmin) >> shift), 1u);
+      t.perm[pos] = (uint16_t)j;
+    }
+    sorter_sync();
     // buckets up to kRankMax ranked in place (every element by its own thread)
     for (uint32_t pos = threadIdx.x; pos < m; pos += kThreads) {
       const uint32_t d = (uint32_t)((sel_key(t, t.perm[pos], sel) - kmin) >> shift);
