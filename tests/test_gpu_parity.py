@@ -168,6 +168,26 @@ def test_all_equal_keys_take_multipass_path():
     assert st["oversize_items"] >= 1
 
 
+def test_long_oversize_item_of_equal_keys():
+    """32M identical keys make one work item far above the tile size, which one CTA
+    merge-sorts in many passes for about a second: the sort kernel's producer warp
+    waits that long for the sorters (its bounded wait restarts while they make
+    progress), and no timeout may be reported.  Equal keys sort stably into input
+    order, so the output must equal the input."""
+    n = 32_000_000
+    d = torch.zeros((n, 100), dtype=torch.uint8, device="cuda")
+    d[:, :10] = torch.tensor(list(b"SAME KEY!!"), dtype=torch.uint8, device="cuda")
+    idx = torch.arange(n, dtype=torch.int64, device="cuda")
+    for b in range(8):
+        d[:, 10 + b] = ((idx >> (8 * (7 - b))) & 0xFF).to(torch.uint8)
+    del idx
+    d = d.reshape(-1)
+    out = torch.empty_like(d)
+    st = elsar.sort(d, out, n, elsar.Params(num_partitions=8), stats=True)
+    assert st["oversize_items"] >= 1
+    assert torch.equal(out, d)
+
+
 def test_two_keys_and_tiny_tiles():
     n = 30_000
     rng = np.random.default_rng(1)
