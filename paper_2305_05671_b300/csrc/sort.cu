@@ -25,7 +25,10 @@
 // barriers FULL[b] (sorters arrive, gatherers wait) and EMPTY[b] (gatherers
 // arrive, sorters wait before refilling slot b) order the two groups, every
 // phase of each barrier taking exactly the 256 sorter and the gatherer
-// threads once.
+// threads once.  A last, producer warp finds the next item one ahead of the
+// sorters (the queue claim or the partition's next item, its bounds, an L2
+// prefetch of its pairs) and hands it over through two mbarrier-guarded
+// slots, so that those dependent loads stay off the sorters' path.
 #include "common.cuh"
 
 namespace elsar {
