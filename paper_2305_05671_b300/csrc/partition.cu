@@ -213,7 +213,6 @@ __global__ void __launch_bounds__(kThreads) classify_kernel(const uint8_t* __res
   }
 }
 
-constexpr int kScanThreads = 1024;
 
 constexpr int kTileChunks = 16;  // 32-element chunks per warp and tile of the single-CTA scans
 
@@ -241,51 +240,95 @@ __device__ __forceinline__ void scan_warp_totals(uint32_t* wsum) {
   __syncthreads();
 }
 
-// Single CTA: bin offsets (exclusive scan of the histogram), scatter cursors,
-// max bin.  A tile is kScanThreads x kTileChunks bins; warp w scans chunks of
-// 32 consecutive bins (coalesced) across its part, then the warps' totals
-// are scanned and a running carry joins the tiles.  Each bin is read and
-// written by one thread (hist and cursor may be the same array).
-__global__ void __launch_bounds__(kScanThreads) scan_bins(const uint32_t* hist, uint32_t B,
-                                                          uint32_t* __restrict__ bin_off, uint32_t* cursor,
-                                                          uint32_t* ctrl) {
-  __shared__ uint32_t wsum[33];
-  __shared__ uint32_t carry_sh;
+// Bin offsets (exclusive scan of the histogram), scatter cursors, max bin,
+// in two launches over tiles of kTsTile bins (one CTA each): tile sums, then
+// every CTA adds the sums of the tiles before its own and scans its tile.
+// Warp w of a tile scans chunks of 32 consecutive bins (coalesced) across its
+// 32 * kTileChunks bins, then the warps' totals are scanned.  Each bin is read
+// and written by one thread (hist and cursor may be the same array); no CTA
+// waits for another.
+constexpr int kTsThreads = 256;
+constexpr uint32_t kTsTile = kTsThreads * kTileChunks;  // 4096 bins
+
+// sum of one value per thread over the CTA, returned to every thread
+// (red: 33 words; three barriers, so it may be called again at once)
+__device__ __forceinline__ uint32_t block_sum(uint32_t v, uint32_t* red) {
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int d = 16; d; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t x = lane < (blockDim.x >> 5) ? red[lane] : 0;
+    for (int d = 16; d; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    if (lane == 0) red[32] = x;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+__global__ void __launch_bounds__(kTsThreads) bin_tile_sums(const uint32_t* __restrict__ hist, uint32_t B,
+                                                            uint32_t* __restrict__ tsum, uint32_t* ctrl) {
+  __shared__ uint32_t red[33];
   if (ctrl[kStatusWord]) return;  // classify gave up: nothing downstream runs
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry_sh = 0;
-  uint32_t mx = 0;
-  __syncthreads();
-  for (uint32_t base = 0; base < B; base += kScanThreads * kTileChunks) {
-    const uint32_t w0 = base + warp * 32 * kTileChunks;
-    uint32_t ex[kTileChunks], run = 0;
+  const uint32_t w0 = blockIdx.x * kTsTile + warp * 32 * kTileChunks;
+  uint32_t sum = 0, mx = 0;
 #pragma unroll
-    for (int j = 0; j < kTileChunks; ++j) {
-      const uint32_t q = w0 + j * 32 + lane;
-      const uint32_t h = q < B ? hist[q] : 0;
-      mx = max(mx, h);
-      const uint32_t incl = warp_incl_scan(h);
-      ex[j] = run + incl - h;
-      run += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) wsum[warp] = run;
-    scan_warp_totals(wsum);
-    const uint32_t off = carry_sh + wsum[warp];
-#pragma unroll
-    for (int j = 0; j < kTileChunks; ++j) {
-      const uint32_t q = w0 + j * 32 + lane;
-      if (q < B) {
-        bin_off[q] = off + ex[j];
-        cursor[q] = off + ex[j];
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry_sh += wsum[32];
-    __syncthreads();
+  for (int j = 0; j < kTileChunks; ++j) {
+    const uint32_t q = w0 + j * 32 + lane;
+    const uint32_t h = q < B ? hist[q] : 0;
+    sum += h;
+    mx = max(mx, h);
   }
-  if (threadIdx.x == 0) bin_off[B] = carry_sh;
   for (int d = 16; d; d >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
   if (lane == 0) atomicMax(ctrl + kMaxBin, mx);
+  sum = block_sum(sum, red);
+  if (threadIdx.x == 0) tsum[blockIdx.x] = sum;
+}
+
+__global__ void __launch_bounds__(kTsThreads) bin_tile_scan(const uint32_t* hist, uint32_t B,
+                                                            const uint32_t* __restrict__ tsum,
+                                                            uint32_t* __restrict__ bin_off, uint32_t* cursor,
+                                                            const uint32_t* ctrl) {
+  __shared__ uint32_t wsum[33];
+  if (ctrl[kStatusWord]) return;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t before = 0;  // the bins of the tiles before this one
+  for (uint32_t i = threadIdx.x; i < blockIdx.x; i += kTsThreads) before += tsum[i];
+  before = block_sum(before, wsum);
+  const uint32_t w0 = blockIdx.x * kTsTile + warp * 32 * kTileChunks;
+  uint32_t ex[kTileChunks], run = 0;
+#pragma unroll
+  for (int j = 0; j < kTileChunks; ++j) {
+    const uint32_t q = w0 + j * 32 + lane;
+    const uint32_t h = q < B ? hist[q] : 0;
+    const uint32_t incl = warp_incl_scan(h);
+    ex[j] = run + incl - h;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) wsum[warp] = run;
+  scan_warp_totals(wsum);
+  const uint32_t off = before + wsum[warp];
+#pragma unroll
+  for (int j = 0; j < kTileChunks; ++j) {
+    const uint32_t q = w0 + j * 32 + lane;
+    if (q < B) {
+      bin_off[q] = off + ex[j];
+      cursor[q] = off + ex[j];
+    }
+  }
+  if (threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) bin_off[B] = before + wsum[32];
+}
+
+// hist -> bin_off, cursor (may be hist), max bin; tsum: one word per tile
+// (scratch).  Returns the number of launches.
+uint32_t scan_bins(const uint32_t* hist, uint32_t B, uint32_t* bin_off, uint32_t* cursor, uint32_t* ctrl,
+                   uint32_t* tsum, cudaStream_t st) {
+  const uint32_t T = (B + kTsTile - 1) / kTsTile;
+  bin_tile_sums<<<T, kTsThreads, 0, st>>>(hist, B, tsum, ctrl);
+  bin_tile_scan<<<T, kTsThreads, 0, st>>>(hist, B, tsum, bin_off, cursor, ctrl);
+  return 2;
 }
 
 // Partition cuts.  Paper rule: c_p = p * B / P.  Refined rule: the boundary t
@@ -332,68 +375,95 @@ __global__ void cuts_kernel(const uint32_t* __restrict__ bin_off, uint32_t log2B
   }
 }
 
-// Single CTA: work items = runs of consecutive fine bins.  A bin starts a new
-// item if it starts a partition, is not "small" (> W = cap/2 pairs), follows a
-// bin that is not small, or its start offset enters a new W-window; a run of
-// small bins inside one window holds < 2W = cap pairs.  Oversize bins
-// (> cap pairs) are listed separately.  item_flag becomes the item id of
-// every bin.  Tiles of kScanThreads x kTileChunks bins as in scan_bins, each
-// bin read and written by one thread.
-__global__ void __launch_bounds__(kScanThreads) items_kernel(const uint32_t* __restrict__ bin_off, uint32_t B,
-                                                             uint32_t cap, uint32_t* item_flag, uint32_t* items,
-                                                             uint32_t* oversize, uint32_t* ctrl) {
-  __shared__ uint32_t wsum[33];
-  __shared__ uint32_t carry_sh;
+// Work items = runs of consecutive fine bins.  A bin starts a new item if it
+// starts a partition, is not "small" (> W = cap/2 pairs), follows a bin that
+// is not small, or its start offset enters a new W-window; a run of small
+// bins inside one window holds < 2W = cap pairs.  Oversize bins (> cap pairs)
+// are listed separately.  item_flag becomes the item id of every bin.  The
+// rule looks at a bin and its neighbour only, so the items are found in two
+// launches over tiles of kTsTile bins laid out as in the bin scan: the count
+// of item starts per tile, then every CTA adds the counts of the tiles before
+// its own and numbers its tile's items.
+__device__ __forceinline__ uint32_t starts_item(const uint32_t* __restrict__ bin_off, const uint32_t* item_flag,
+                                                uint32_t q, uint32_t W) {
+  const uint32_t o = bin_off[q], cnt = bin_off[q + 1] - o;
+  if (item_flag[q] != 0 || q == 0 || cnt > W) return 1;
+  const uint32_t po = bin_off[q - 1];
+  return (o - po) > W || (o / W) != (po / W);
+}
+
+__global__ void __launch_bounds__(kTsThreads) item_tile_counts(const uint32_t* __restrict__ bin_off, uint32_t B,
+                                                               uint32_t cap, const uint32_t* __restrict__ item_flag,
+                                                               uint32_t* __restrict__ tcnt, const uint32_t* ctrl) {
+  __shared__ uint32_t red[33];
   if (ctrl[kStatusWord]) return;
   const uint32_t W = cap / 2;
   const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry_sh = 0;
-  __syncthreads();
-  for (uint32_t base = 0; base < B; base += kScanThreads * kTileChunks) {
-    const uint32_t w0 = base + warp * 32 * kTileChunks;
-    uint32_t ex[kTileChunks], run = 0, fl = 0;  // fl bit j: bin of chunk j starts an item
+  const uint32_t w0 = blockIdx.x * kTsTile + warp * 32 * kTileChunks;
+  uint32_t n = 0;
 #pragma unroll
-    for (int j = 0; j < kTileChunks; ++j) {
-      const uint32_t q = w0 + j * 32 + lane;
-      uint32_t f = 0;
-      if (q < B) {
-        const uint32_t o = bin_off[q], cnt = bin_off[q + 1] - o;
-        f = item_flag[q] != 0 || q == 0 || cnt > W;
-        if (!f) {
-          const uint32_t po = bin_off[q - 1];
-          f = (o - po) > W || (o / W) != (po / W);
-        }
-      }
-      fl |= f << j;
-      const uint32_t incl = warp_incl_scan(f);
-      ex[j] = run + incl - f;
-      run += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) wsum[warp] = run;
-    scan_warp_totals(wsum);
-    const uint32_t off = carry_sh + wsum[warp];
+  for (int j = 0; j < kTileChunks; ++j) {
+    const uint32_t q = w0 + j * 32 + lane;
+    if (q < B) n += starts_item(bin_off, item_flag, q, W);
+  }
+  n = block_sum(n, red);
+  if (threadIdx.x == 0) tcnt[blockIdx.x] = n;
+}
+
+__global__ void __launch_bounds__(kTsThreads) item_tile_write(const uint32_t* __restrict__ bin_off, uint32_t B,
+                                                              uint32_t cap, uint32_t* item_flag, uint32_t* items,
+                                                              uint32_t* oversize, const uint32_t* __restrict__ tcnt,
+                                                              uint32_t* ctrl) {
+  __shared__ uint32_t wsum[33];
+  if (ctrl[kStatusWord]) return;
+  const uint32_t W = cap / 2;
+  const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t before = 0;  // the items of the tiles before this one
+  for (uint32_t i = threadIdx.x; i < blockIdx.x; i += kTsThreads) before += tcnt[i];
+  before = block_sum(before, wsum);
+  const uint32_t w0 = blockIdx.x * kTsTile + warp * 32 * kTileChunks;
+  uint32_t ex[kTileChunks], run = 0, fl = 0;  // fl bit j: bin of chunk j starts an item
 #pragma unroll
-    for (int j = 0; j < kTileChunks; ++j) {
-      const uint32_t q = w0 + j * 32 + lane;
-      if (q < B) {
-        const uint32_t id = off + ex[j];
-        if ((fl >> j) & 1) {
-          items[id] = q;
-          if (bin_off[q + 1] - bin_off[q] > cap) oversize[atomicAdd(ctrl + kNumOversize, 1u)] = id;
-          item_flag[q] = id;
-        } else {
-          item_flag[q] = id - 1;
-        }
+  for (int j = 0; j < kTileChunks; ++j) {
+    const uint32_t q = w0 + j * 32 + lane;
+    const uint32_t f = q < B ? starts_item(bin_off, item_flag, q, W) : 0;
+    fl |= f << j;
+    const uint32_t incl = warp_incl_scan(f);
+    ex[j] = run + incl - f;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) wsum[warp] = run;
+  scan_warp_totals(wsum);
+  const uint32_t off = before + wsum[warp];
+#pragma unroll
+  for (int j = 0; j < kTileChunks; ++j) {
+    const uint32_t q = w0 + j * 32 + lane;
+    if (q < B) {
+      const uint32_t id = off + ex[j];
+      if ((fl >> j) & 1) {
+        items[id] = q;
+        if (bin_off[q + 1] - bin_off[q] > cap) oversize[atomicAdd(ctrl + kNumOversize, 1u)] = id;
+        item_flag[q] = id;
+      } else {
+        item_flag[q] = id - 1;
       }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) carry_sh += wsum[32];
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    items[carry_sh] = B;
-    ctrl[kNumItems] = carry_sh;
+  if (threadIdx.x == 0 && blockIdx.x == gridDim.x - 1) {
+    const uint32_t total = before + wsum[32];
+    items[total] = B;
+    ctrl[kNumItems] = total;
   }
+}
+
+// items, item_flag (partition starts in, item ids out), oversize list, item
+// count; tcnt: one word per tile (scratch).  Returns the number of launches.
+uint32_t find_items(const uint32_t* bin_off, uint32_t B, uint32_t cap, uint32_t* item_flag, uint32_t* items,
+                    uint32_t* oversize, uint32_t* ctrl, uint32_t* tcnt, cudaStream_t st) {
+  const uint32_t T = (B + kTsTile - 1) / kTsTile;
+  item_tile_counts<<<T, kTsThreads, 0, st>>>(bin_off, B, cap, item_flag, tcnt, ctrl);
+  item_tile_write<<<T, kTsThreads, 0, st>>>(bin_off, B, cap, item_flag, items, oversize, tcnt, ctrl);
+  return 2;
 }
 
 // Coarse offsets: seg[c][b] (counts of classify CTA b in coarse bin c) becomes
@@ -832,19 +902,19 @@ cudaError_t partition_batch(const BatchPartArgs& a) {
   if (cshift > kStagedMaxShift) {  // bins too many for whole runs: one atomic pass
     classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.km, a.poff, a.K, a.splitters, a.tbase, a.log2B,
                                                  a.pairs_in_order, a.cursor, 0, nullptr, 0);
-    scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
+    *a.launches += scan_bins(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl, a.items, st);
     scatter_atomic_kernel<<<G, kThreads, 0, st>>>(a.pairs_in_order, a.N, a.poff, a.K, a.cursor, a.pairs, a.ctrl);
     mark_set_starts<<<(a.K + 255) / 256, 256, 0, st>>>(a.tbase, a.K, a.item_flag);
-    items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize,
-                                             a.ctrl);
-    *a.launches += 5;
+    // the cursors are spent: they hold the item scan's tile counts
+    *a.launches += find_items(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize, a.ctrl, a.cursor, st);
+    *a.launches += 3;
     return cudaGetLastError();
   }
   // roles: input-order pairs and the final bin order share `pairs`; the
   // coarse order between the two passes lives in `pairs_in_order`
   classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.km, a.poff, a.K, a.splitters, a.tbase, a.log2B, a.pairs,
                                                a.cursor, cshift, a.seg_hist, (uint32_t)segs);
-  scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl);
+  *a.launches += scan_bins(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl, a.items, st);
   coarse_offsets_kernel<<<(C + 7) / 8, 256, 0, st>>>(a.seg_hist, (uint32_t)segs, G, C, cshift, a.bin_off, a.ctrl);
   coarse_scatter_kernel<<<G, kStageThreads, stage_smem_bytes(C), st>>>(a.pairs, a.N, ilog2(kThreads), 0, a.seg_hist,
                                                                         (uint32_t)segs, cshift, C, a.pairs_in_order,
@@ -853,8 +923,8 @@ cudaError_t partition_batch(const BatchPartArgs& a) {
                                                                                  cshift, a.pairs, a.ctrl,
                                                                                  kWaitLimitCycles);
   mark_set_starts<<<(a.K + 255) / 256, 256, 0, st>>>(a.tbase, a.K, a.item_flag);
-  items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize, a.ctrl);
-  *a.launches += 7;
+  *a.launches += find_items(a.bin_off, a.B, a.tile_pairs, a.item_flag, a.items, a.oversize, a.ctrl, a.cursor, st);
+  *a.launches += 5;
   return cudaGetLastError();
 }
 
@@ -894,7 +964,7 @@ cudaError_t partition_records(const PartArgs& a) {
                                             a.seg_hist, (uint32_t)segs);
   }
   if (a.ev[0]) cudaEventRecord(a.ev[0], st);
-  scan_bins<<<1, kScanThreads, 0, st>>>(a.cursor, B, a.bin_off, a.cursor, a.ctrl);
+  *a.launches += scan_bins(a.cursor, B, a.bin_off, a.cursor, a.ctrl, a.items, st);
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       nullptr);
   if (a.ev[1]) cudaEventRecord(a.ev[1], st);
@@ -902,7 +972,7 @@ cudaError_t partition_records(const PartArgs& a) {
     scatter_atomic_kernel<<<(unsigned)sms * 8, kThreads, 0, st>>>(pin, a.n, nullptr, 0, a.cursor,
                                                                 static_cast<Pair*>(a.pairs), a.ctrl);
     if (a.ev[2]) cudaEventRecord(a.ev[2], st);
-    *a.launches += 4;
+    *a.launches += 3;
     return cudaGetLastError();
   }
   // two scatter passes through shared memory: coarse bins, then fine bins inside each
@@ -918,7 +988,7 @@ cudaError_t partition_records(const PartArgs& a) {
   fine_scatter_kernel<<<C, kStageThreads, smem2, st>>>(static_cast<const Pair*>(a.mid), a.bin_off, B, cshift,
                                                         static_cast<Pair*>(a.pairs), a.ctrl, a.wait_limit);
   if (a.ev[2]) cudaEventRecord(a.ev[2], st);
-  *a.launches += 6;
+  *a.launches += 5;
   return cudaGetLastError();
 }
 
@@ -946,10 +1016,10 @@ cudaError_t classify_accumulate(const PartArgs& a) {
 
 cudaError_t scan_and_cut(const PartArgs& a) {
   const uint32_t B = 1u << a.log2B;
-  scan_bins<<<1, kScanThreads, 0, a.stream>>>(a.cursor, B, a.bin_off, a.cursor, a.ctrl);
+  *a.launches += scan_bins(a.cursor, B, a.bin_off, a.cursor, a.ctrl, a.items, a.stream);
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, a.stream>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts,
                                                            a.part_off, nullptr);
-  *a.launches += 2;
+  *a.launches += 1;
   return cudaGetLastError();
 }
 
@@ -960,9 +1030,9 @@ cudaError_t build_items(const PartArgs& a) {
   cudaMemsetAsync(a.ctrl, 0, 3 * sizeof(uint32_t), st);  // item count, oversize count, queue head
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       a.item_flag);
-  items_kernel<<<1, kScanThreads, 0, st>>>(a.bin_off, B, a.tile_pairs, a.item_flag, a.items, a.oversize,
-                                           a.ctrl);
-  *a.launches += 2;
+  // the scatter cursors are spent: they hold the item scan's tile counts
+  *a.launches += find_items(a.bin_off, B, a.tile_pairs, a.item_flag, a.items, a.oversize, a.ctrl, a.cursor, st);
+  *a.launches += 1;
   return cudaGetLastError();
 }
 
