@@ -186,16 +186,31 @@ constexpr int kMergeTile = 2048;
 constexpr int kMergeThreads = 256;
 constexpr int kMergeItems = kMergeTile / kMergeThreads;
 
-// number of elements taken from a among the first diag outputs of merge(a, b)
-__device__ __forceinline__ uint64_t merge_split(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb,
-                                                uint64_t diag) {
-  uint64_t lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;
-  while (lo < hi) {
-    uint64_t mid = (lo + hi) >> 1;
-    if (a[mid] <= b[diag - 1 - mid]) lo = mid + 1;
-    else hi = mid;
+// Number of elements taken from a among the first diag outputs of merge(a, b)
+// (the largest i with a[i - 1] <= b[diag - i], ties to a), found by one warp:
+// each round tests 32 evenly spaced candidates at once (one load per lane)
+// and keeps the segment where the predicate a[mid] <= b[diag - 1 - mid] turns
+// false, so the dependent loads fall from log2 of the range to about log32 of
+// it.  Returned to every lane.
+__device__ __forceinline__ uint64_t warp_merge_split(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb,
+                                                     uint64_t diag) {
+  const uint32_t lane = threadIdx.x & 31;
+  uint64_t lo = diag > nb ? diag - nb : 0, hi = diag < na ? diag : na;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const uint64_t step = (hi - lo + 31) / 32;
+    const uint64_t mid = lo + lane * step;  // lane 0 tests lo itself
+    const bool t = mid < hi && a[mid] <= b[diag - 1 - mid];
+    const uint32_t m = __ballot_sync(0xffffffffu, t);  // candidates below the answer
+    const uint32_t k = 32 - __clz(m);                   // the first candidate that fails (or 32)
+    // the predicate is true before the answer and false from it on
+    const uint64_t nlo = k ? lo + (uint64_t)(k - 1) * step + 1 : lo;
+    const uint64_t nhi = k < 32 ? min(hi, lo + (uint64_t)k * step) : hi;
+    lo = nlo;
+    hi = nhi;
   }
-  return lo;
+  const uint64_t mid = lo + lane;
+  const bool t = mid < hi && a[mid] <= b[diag - 1 - mid];
+  return lo + __popc(__ballot_sync(0xffffffffu, t));
 }
 
 __global__ void __launch_bounds__(kMergeThreads) merge_pass_u64(const uint64_t* __restrict__ src,
@@ -207,9 +222,10 @@ __global__ void __launch_bounds__(kMergeThreads) merge_pass_u64(const uint64_t* 
   const uint64_t p0 = (o0 / (2 * w)) * (2 * w);
   const uint64_t a0 = p0, a1 = min(S, p0 + w), b0 = a1, b1 = min(S, p0 + 2 * w);
   __shared__ uint64_t split[2];
-  if (threadIdx.x < 2) {
-    uint64_t diag = (threadIdx.x ? o1 : o0) - p0;
-    split[threadIdx.x] = merge_split(src + a0, a1 - a0, src + b0, b1 - b0, diag);
+  if (threadIdx.x < 64) {  // warp 0: the window's start, warp 1: its end
+    const uint32_t w = threadIdx.x >> 5;
+    const uint64_t r = warp_merge_split(src + a0, a1 - a0, src + b0, b1 - b0, (w ? o1 : o0) - p0);
+    if ((threadIdx.x & 31) == 0) split[w] = r;
   }
   __syncthreads();
   const uint64_t ka0 = split[0], ka1 = split[1];
