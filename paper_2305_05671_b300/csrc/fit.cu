@@ -157,29 +157,73 @@ __global__ void sample_kernel(const uint8_t* __restrict__ rec, uint64_t n, uint6
 constexpr int kChunk = 4096;
 constexpr int kChunkThreads = 1024;
 
+// Bitonic sort of one chunk of kChunk keys (padding ~0 past S), 4 keys per
+// thread in registers (element e = 4 * thread + r): compare-exchange stages
+// with partners 1 or 2 apart stay in the thread, 4 to 64 apart go through warp
+// shuffles, 128 and more through shared memory, so only those take barriers.
 __global__ void __launch_bounds__(kChunkThreads) chunk_sort_u64(uint64_t* data, uint64_t S) {
+  static_assert(kChunk == 4 * kChunkThreads, "four keys per thread");
   __shared__ uint64_t s[kChunk];
   const uint64_t base = (uint64_t)blockIdx.x * kChunk;
-  for (int i = threadIdx.x; i < kChunk; i += kChunkThreads) s[i] = base + i < S ? data[base + i] : ~0ull;
-  __syncthreads();
-  for (int k = 2; k <= kChunk; k <<= 1) {
-    for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int i = threadIdx.x; i < kChunk; i += kChunkThreads) {
-        int ixj = i ^ j;
-        if (ixj > i) {
-          uint64_t a = s[i], b = s[ixj];
-          bool up = (i & k) == 0;
-          if ((a > b) == up) {
-            s[i] = b;
-            s[ixj] = a;
+  const uint32_t t = threadIdx.x;
+  uint64_t v[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t g = base + 4 * t + r;
+    v[r] = g < S ? data[g] : ~0ull;
+  }
+  for (uint32_t k = 2; k <= (uint32_t)kChunk; k <<= 1) {
+    uint32_t j = k >> 1;
+    if (j >= 128) {  // partners in other warps: through shared memory
+      __syncthreads();  // the previous read-back is done
+#pragma unroll
+      for (int r = 0; r < 4; ++r) s[4 * t + r] = v[r];
+      __syncthreads();
+      for (; j >= 128; j >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // kChunk / 2 pairs, two per thread
+          const uint32_t p = t + q * kChunkThreads;
+          const uint32_t e = ((p & ~(j - 1)) << 1) | (p & (j - 1)), f = e | j;
+          const uint64_t x = s[e], y = s[f];
+          if ((x > y) == ((e & k) == 0)) {
+            s[e] = y;
+            s[f] = x;
           }
         }
+        __syncthreads();
       }
-      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[r] = s[4 * t + r];
     }
+    for (; j >= 4; j >>= 1) {  // partners in this warp, j / 4 lanes away
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const uint32_t e = 4 * t + r;
+        const uint64_t w = __shfl_xor_sync(0xffffffffu, v[r], j >> 2);
+        const bool keep_min = ((e & j) == 0) == ((e & k) == 0);
+        v[r] = keep_min ? min(v[r], w) : max(v[r], w);
+      }
+    }
+    // partners in this thread: j = 2 (when k >= 4), then j = 1
+    auto cx = [&](uint64_t& x, uint64_t& y, uint32_t e) {  // e: the lower element
+      if ((x > y) == ((e & k) == 0)) {
+        const uint64_t z = x;
+        x = y;
+        y = z;
+      }
+    };
+    if (j == 2) {
+      cx(v[0], v[2], 4 * t);
+      cx(v[1], v[3], 4 * t + 1);
+    }
+    cx(v[0], v[1], 4 * t);
+    cx(v[2], v[3], 4 * t + 2);
   }
-  for (int i = threadIdx.x; i < kChunk; i += kChunkThreads)
-    if (base + i < S) data[base + i] = s[i];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const uint64_t g = base + 4 * t + r;
+    if (g < S) data[g] = v[r];
+  }
 }
 
 constexpr int kMergeTile = 2048;
