@@ -55,6 +55,37 @@ __device__ __forceinline__ uint32_t route_u(const DNode& v, uint64_t u) {
 
 __device__ __forceinline__ uint32_t route(const DNode& v, uint64_t x) { return route_u(v, local_u(v, x)); }
 
+// The router of a finished internal node, decided in FP32 where that is
+// safe.  The node keeps A = a c and B = b c rounded to FP32 in h (which only
+// leaves use otherwise), and t32 = fma(A, u, B) in FP32.  With A, B and u
+// each rounded once to FP32 and one rounded fma, |t32 - t64| <=
+// (|A u| + |B|) 2^-21, t64 being route_u's FP64 value (whose own rounding is
+// below 2^-50 of the same terms).  The screen keeps twice that margin plus
+// 2^-30 and answers only when the whole interval around t32 takes the same
+// branch of route_u (0, fanout - 1, or one floor); otherwise, and for any
+// inf or NaN, it returns route_u's FP64 result, so every decision is route_u's.
+__device__ __forceinline__ void set_route_screen(DNode& v) {
+  const float A = __double2float_rn(__dmul_rn(v.a, v.c)), B = __double2float_rn(__dmul_rn(v.b, v.c));
+  v.h = __hiloint2double(__float_as_int(B), __float_as_int(A));
+}
+
+__device__ __forceinline__ uint32_t route_screened(const DNode& v, uint64_t x) {
+  const uint64_t u = local_u(v, x);
+  const float A = __int_as_float(__double2loint(v.h)), B = __int_as_float(__double2hiint(v.h));
+  const float uf = __ull2float_rn(u);
+  const float t = __fmaf_rn(A, uf, B);
+  const float err = __fmaf_rn(__fadd_rn(fabsf(__fmul_rn(A, uf)), fabsf(B)), 0x1p-20f, 0x1p-30f);
+  const float lo = __fsub_rn(t, err), hi = __fadd_rn(t, err);
+  const float F = __uint2float_rn(v.fanout);  // exact: fanouts are far below 2^24
+  if (hi <= 0.0f) return 0;
+  if (lo >= F) return v.fanout - 1;
+  if (lo > 0.0f && hi < F) {
+    const float fl = floorf(lo);
+    if (fl == floorf(hi)) return (uint32_t)fl;
+  }
+  return route_u(v, u);
+}
+
 // Smallest u in (a, b] with f(u) >= q for a monotone f with f(a) < q <=
 // f(b): a gallop from the guess m (it only sets the start; m > b: none, the
 // middle is taken), then a bisection.  Every decision evaluates f exactly.
@@ -413,7 +444,7 @@ __global__ void __launch_bounds__(256) level_sums(const uint64_t* __restrict__ x
       if (kRoute && v != kSettled) {
         const DNode& nd = nodes[v];
         if (nd.fanout) {
-          const uint32_t ch = nd.child0 + route(nd, x[k]);
+          const uint32_t ch = nd.child0 + route_screened(nd, x[k]);
           pnode[k] = ch;
           v = ch;
         } else {
@@ -645,6 +676,7 @@ __global__ void level_finalize(DNode* nodes, const uint32_t* __restrict__ fc, co
       nd.fanout = fc[i];
       nd.child0 = lv1 + childoff[i];
       nd.c = __ddiv_rn(__uint2double_rn(nd.fanout), __uint2double_rn(nd.e - nd.s));
+      set_route_screen(nd);
     } else {
       const SetInfo si = sets[nd.depth_set >> 8];
       const double dS = __ull2double_rn(si.S);
@@ -674,7 +706,7 @@ __device__ __forceinline__ uint32_t first_routed(const uint64_t* __restrict__ x,
   uint32_t lo = nd.s, hi = nd.e;
   while (lo < hi) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (route(nd, x[mid]) >= cc) hi = mid;
+    if (route_screened(nd, x[mid]) >= cc) hi = mid;
     else lo = mid + 1;
   }
   return lo;
@@ -791,14 +823,14 @@ __device__ __forceinline__ uint64_t bin_lower_bound(const DNode* __restrict__ no
   DNode v = nodes[root];
   while (lo < hi) {
     while (v.fanout) {
-      const uint32_t c = route(v, lo);
-      if (c != route(v, hi)) break;
+      const uint32_t c = route_screened(v, lo);
+      if (c != route_screened(v, hi)) break;
       v = nodes[v.child0 + c];
     }
     if (!v.fanout) return leaf_lower_bound(v, lo, hi, q, log2B);
     const uint64_t mid = lo + ((hi - lo) >> 1);
-    DNode w = nodes[v.child0 + route(v, mid)];
-    while (w.fanout) w = nodes[w.child0 + route(w, mid)];
+    DNode w = nodes[v.child0 + route_screened(v, mid)];
+    while (w.fanout) w = nodes[w.child0 + route_screened(w, mid)];
     if (leaf_bin(w, mid, log2B) >= q) hi = mid;
     else lo = mid + 1;
   }
