@@ -42,7 +42,18 @@ def _resolved_log2B(n, P):
 
 @pytest.mark.parametrize("name", list(SPECS))
 def test_model_bit_identical_to_oracle(name):
-    n, S, seed = 200_000, 5000, 77
+    _check_model(name, 200_000, 5000, 77)
+
+
+@pytest.mark.parametrize("name", ["uniform", "zipf13", "prefix"])
+def test_large_sample_model_bit_identical_to_oracle(name):
+    """A 200K-point sample: wide trees (uniform keys) and deep ones (skewed keys),
+    with many routing decisions near child boundaries, where the routers' FP32
+    screen must hand over to FP64."""
+    _check_model(name, 4_000_000, 200_000, 91)
+
+
+def _check_model(name, n, S, seed):
     host = recgen.generate_cpu(n, SPECS[name])
     p = elsar.Params(num_partitions=64, sample_size=S, seed=seed)
     _, _, model = _fit(host, p, n)
