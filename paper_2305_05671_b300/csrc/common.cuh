@@ -354,7 +354,7 @@ struct PartArgs {
 // kMaxCoarse of them; classify CTAs (at most kMaxSegments) count per coarse bin.
 constexpr uint32_t kMaxCoarse = 512;
 constexpr uint32_t kMaxFineShift = 11;    // at most 2^11 fine bins per coarse bin (shared-memory cursors)
-constexpr uint32_t kStagedMaxShift = 9;   // above 2^9 fine bins per coarse bin the runs get too short to stage
+constexpr uint32_t kStagedMaxShift = kMaxFineShift;  // beyond it the fine pass's cursors do not fit: one atomic pass
 constexpr uint32_t kMaxSegments = 2048;
 inline uint32_t coarse_shift(uint32_t log2B) { return log2B > 9 ? log2B - 9 : 0; }
 inline uint64_t coarse_segments(uint64_t n) {

@@ -847,9 +847,10 @@ __global__ void __launch_bounds__(kThreads) classify_batch_kernel(const uint8_t*
 }
 
 // Pass B in one step, for fine-bin spaces too large for the two staged
-// passes to write whole runs (more than 2^kStagedMaxShift fine bins per
-// coarse bin): slot from an atomic cursor per bin; the record index (inside
-// its set when poff is given) replaces the fine bin.
+// passes (more than 2^kStagedMaxShift fine bins per coarse bin: the fine
+// pass's cursors would not fit in shared memory): slot from an atomic cursor
+// per bin; the record index (inside its set when poff is given) replaces the
+// fine bin.
 __global__ void __launch_bounds__(kThreads) scatter_atomic_kernel(const Pair* __restrict__ in, uint64_t N,
                                                                   const uint64_t* __restrict__ poff, uint32_t K,
                                                                   uint32_t* __restrict__ cursor, Pair* __restrict__ out,
@@ -889,6 +890,11 @@ static void coarse_of(uint64_t B, uint32_t* cshift, uint32_t* C) {
   *C = (uint32_t)((B + (1ull << s) - 1) >> s);
 }
 
+// Many record sets: one atomic pass above 2^9 fine bins per coarse bin (the
+// batched workload measured faster that way than with the staged passes up
+// to kStagedMaxShift, which a single large set prefers).
+constexpr uint32_t kBatchStagedMaxShift = 9;
+
 cudaError_t partition_batch(const BatchPartArgs& a) {
   cudaStream_t st = a.stream;
   const int sms = sm_count();
@@ -899,7 +905,7 @@ cudaError_t partition_batch(const BatchPartArgs& a) {
   coarse_of(a.B, &cshift, &C);
   const uint64_t segs = coarse_segments(a.N);
   const unsigned G = (unsigned)umin64(segs, (uint64_t)sms * 8);
-  if (cshift > kStagedMaxShift) {  // bins too many for whole runs: one atomic pass
+  if (cshift > kBatchStagedMaxShift) {  // many sets: one atomic pass
     classify_batch_kernel<<<G, kThreads, 0, st>>>(a.ins, a.km, a.poff, a.K, a.splitters, a.tbase, a.log2B,
                                                  a.pairs_in_order, a.cursor, 0, nullptr, 0);
     *a.launches += scan_bins(a.cursor, a.B, a.bin_off, a.cursor, a.ctrl, a.items, st);
@@ -968,7 +974,7 @@ cudaError_t partition_records(const PartArgs& a) {
   cuts_kernel<<<(a.P + 1 + 255) / 256, 256, 0, st>>>(a.bin_off, a.log2B, a.P, (int)a.balance, a.cuts, a.part_off,
                                                       nullptr);
   if (a.ev[1]) cudaEventRecord(a.ev[1], st);
-  if (cshift > kStagedMaxShift) {  // bins too many for whole runs: one atomic pass
+  if (cshift > kStagedMaxShift) {  // more fine bins per coarse bin than the fine pass holds: one atomic pass
     scatter_atomic_kernel<<<(unsigned)sms * 8, kThreads, 0, st>>>(pin, a.n, nullptr, 0, a.cursor,
                                                                 static_cast<Pair*>(a.pairs), a.ctrl);
     if (a.ev[2]) cudaEventRecord(a.ev[2], st);

@@ -68,16 +68,33 @@ def test_batch_rejects_bad_sets():
         elsar.Batch([d, torch.zeros(0, dtype=torch.uint8, device="cuda")], [d, d])
 
 
-def test_batch_beyond_staged_bin_space_matches_oracle():
+def test_batch_large_bin_space_matches_oracle():
     """More than 2^18 fine bins over all sets (4200 sets of 1,000-1,600 records,
-    64 bins each) take the one-pass atomic scatter instead of the two staged
-    passes; every set still equals the oracle's stable sort."""
+    64 bins each): more than 2^9 fine bins per coarse bin, where many sets take
+    the one-pass atomic scatter; every set still equals the oracle's stable
+    sort."""
     K = 4200
     sizes = [1000 + (recgen.h(9, k, 0, 0) % 600) for k in range(K)]
     hosts = [recgen.generate_cpu(n, recgen.batch_spec(k)) for k, n in enumerate(sizes)]
     b, d_ins, d_outs = _run(hosts, elsar.Params(tile_pairs=2048, seed=19))
     info = b.info()
     assert info["total_bins"] > (1 << 18) and info["total_records"] == sum(sizes)
+    for k, h in enumerate(hosts):
+        assert np.array_equal(d_outs[k].cpu().numpy(), oracle.stable_sort(h)), k
+    b.close()
+
+
+def test_batch_atomic_bin_space_matches_oracle():
+    """More than 2^20 fine bins over all sets (17,000 sets of 60-120 records,
+    64 bins each): the one-pass atomic scatter over more than 2^11 fine bins
+    per coarse bin, with every record's index taken inside its own set; every
+    set still equals the oracle's stable sort."""
+    K = 17000
+    sizes = [60 + (recgen.h(11, k, 0, 0) % 61) for k in range(K)]
+    hosts = [recgen.generate_cpu(n, recgen.batch_spec(k)) for k, n in enumerate(sizes)]
+    b, d_ins, d_outs = _run(hosts, elsar.Params(tile_pairs=2048, seed=23))
+    info = b.info()
+    assert info["total_bins"] > (1 << 20) and info["total_records"] == sum(sizes)
     for k, h in enumerate(hosts):
         assert np.array_equal(d_outs[k].cpu().numpy(), oracle.stable_sort(h)), k
     b.close()

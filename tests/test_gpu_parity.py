@@ -179,6 +179,14 @@ def test_all_equal_keys_take_multipass_path():
     assert st["oversize_items"] >= 1
 
 
+def test_fine_bins_beyond_the_staged_scatter():
+    """2^21 fine bins (2^12 per coarse bin, more than the staged fine pass
+    holds) take the one-pass atomic scatter; the output equals the oracle's."""
+    n = 300_000
+    host = recgen.generate_cpu(n, SPECS["zipf11"])
+    _check_plain(host, n, elsar.Params(num_partitions=64, fine_bins_log2=21, seed=n))
+
+
 def test_long_oversize_item_of_equal_keys():
     """32M identical keys make one work item far above the tile size, which one CTA
     merge-sorts in many passes for about a second: the sort kernel's producer warp
