@@ -602,7 +602,7 @@ def run_cfg4(args, dev, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="elsar", choices=["elsar", "reference"])
     ap.add_argument("--tile-pairs", type=int, default=0)
